@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: free-space Poisson solve throughput (grid cells solved / s).
+
+One step = one full solve (five passes) of the 256^3-cell FP32 workload:
+64 seeded Plummer spheres plus a 1 % uniform background, unit spacing, G = 1,
+padded to 512^3.  Inputs are resident in HBM before timing; L2 is flushed
+(256 MiB write) between steps outside the timed events.  Each rank solves
+its own independent field (weak scaling, no data-path collective).
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the FP64 CPU
+oracle (FFT-convolution route) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid cells solved/sec and % of HBM roofline at stated rel-L2 vs FP64 oracle"
+UNIT = "cells/s"
+PASS_NAMES = ["x_fwd", "y_fwd", "z_conv", "y_inv", "x_inv"]
+KERNEL_NAMES = ["k_x_fwd", "k_y_fwd", "k_z_conv", "k_y_inv", "k_x_inv"]
+TOL_REL_L2 = 1e-6
+
+WORKLOADS = {
+    "plummer256": dict(n=256, desc="256^3 cells FP32, 64 seeded Plummer spheres + 1% uniform "
+                       "background, unit spacing, G=1, zero-padded to 512^3"),
+    "lognormal512": dict(n=512, desc="512^3 cells FP32, seeded lognormal field (sigma 1.5, "
+                         "k^-3 spectrum) + uniform ball r=40, zero-padded to 1024^3"),
+}
+
+
+def make_density(name, seed):
+    import workloads
+    n = WORKLOADS[name]["n"]
+    if name == "plummer256":
+        rho, _ = workloads.plummer_spheres(n, count=64, seed=seed)
+    else:
+        rho, _ = workloads.lognormal_field(n, seed=seed)
+    return rho.astype(np.float32)
+
+
+def pass_bytes(nx, ny, nz, rsize=4):
+    """Algorithmic HBM bytes of each pass (read + write, octant Ghat)."""
+    c = 2 * rsize
+    cells = nx * ny * nz
+    w1 = (nx + 1) * ny * nz * c
+    w2 = (nx + 1) * 2 * ny * nz * c
+    g = (nx + 1) * (ny + 1) * (nz + 1) * rsize
+    return [cells * rsize + w1, w1 + w2, 2 * w2 + g, w2 + w1, w1 + cells * rsize]
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_02294_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """dram bytes/launch from a committed ncu summary, if it was taken on the
+    current kernel sources (profiles/*.md lines 'traffic: <kernel> <workload>
+    <bytes> source=<hash>')."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    cur = source_hash()
+    pat = re.compile(r"^traffic:\s+(\S+)\s+(\S+)\s+(\d+)\s+source=(\w+)", re.M)
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for m in pat.finditer(open(os.path.join(pdir, fn)).read()):
+            if m.group(1) == kernel and m.group(2) == workload and m.group(4) == cur:
+                return int(m.group(3))
+    return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "20", "-i", str(self.gpu_id)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def cpu_oracle_time(rho32, reps, min_seconds):
+    """Time the FP64 oracle (FFT-convolution route, all host cores)."""
+    import oracle
+    rho = rho32.astype(np.float64)
+    times = []
+    out = None
+    t_start = time.perf_counter()
+    while len(times) < reps or (time.perf_counter() - t_start) < min_seconds:
+        t0 = time.perf_counter()
+        out = oracle.solve_fft(rho, workers=-1)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= 20:
+            break
+    return times, out
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = args.workload
+    n = WORKLOADS[wl]["n"]
+    rho32 = make_density(wl, args.seed)
+    import oracle
+    rho = rho32.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.solve_fft(rho, workers=-1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.solve_fft(rho, workers=-1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * n ** 3 / total
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl, "description": WORKLOADS[wl]["desc"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "full %d^3 field per step, oracle FFT-convolution route "
+                                   "(scipy.fft FP64, workers=all cores)" % n},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2409_02294_gb300 as pg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = args.workload
+    n = WORKLOADS[wl]["n"]
+    rho32 = make_density(wl, args.seed + rank)
+    rho = torch.from_numpy(rho32).to(dev)
+    phi = torch.empty_like(rho)
+    plan = pg.Plan(n, n, n, precision="fp32")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(evs=None):
+        if evs is None:
+            for i in range(5):
+                plan.solve_pass(i, rho, phi, stream)
+            return
+        evs[0].record(stream)
+        for i in range(5):
+            plan.solve_pass(i, rho, phi, stream)
+            evs[i + 1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = "GPU-" + str(props.uuid) if hasattr(props, "uuid") else str(dev.index)
+    sampler = ClockSampler(gpu_id)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(events[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clocks = sampler.stop()
+
+    step_ms = [ev[0].elapsed_time(ev[5]) for ev in events]
+    pass_ms = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in events) / args.steps for i in range(5)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells = n ** 3
+    value = world * cells * args.steps / (total_ms / 1e3)
+
+    # accuracy of this run's output against the FP64 oracle, and the oracle
+    # timed on the host cores (rank 0, N = 1 only)
+    cpu = None
+    acc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, ref = cpu_oracle_time(rho32, reps=2, min_seconds=8.0)
+        out = phi.double().cpu().numpy()
+        acc = {"rel_l2": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
+               "max_rel": float(np.abs(out - ref).max() / np.abs(ref).max()),
+               "tolerance_rel_l2": TOL_REL_L2, "reference": "FP64 oracle, full field"}
+        cpu = {"value": cells / statistics.median(times), "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "full %d^3 field, oracle FFT-convolution route (scipy.fft FP64, all "
+                         "host cores), %d solves, median" % (n, len(times))}
+
+    # end to end through the C-ABI host-buffer call: H2D + solve + D2H per step
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(rho32).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        for _ in range(3):
+            plan.solve_host(host_in, host_out, stream)
+        ksteps = max(3, min(args.steps, 50))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            plan.solve_host(host_in, host_out, stream)
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * cells * ksteps / te, "unit": UNIT,
+               "h2d_bytes_per_step": rho32.nbytes, "d2h_bytes_per_step": rho32.nbytes,
+               "steps": ksteps}
+
+    dom = int(np.argmax(pass_ms))
+    pb = pass_bytes(n, n, n)
+    peak, peak_kind = peaks()
+    achieved = pb[dom] / (pass_ms[dom] / 1e3) / 1e9
+    traffic = profiled_traffic(KERNEL_NAMES[dom], wl)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl, "description": WORKLOADS[wl]["desc"],
+                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                       "parallelism": "independent field per GPU" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                         if peak_kind == "measured" else "fallback 6800 GB/s",
+                         "traffic": traffic, "algorithmic_bytes": pb[dom]},
+            "passes": {PASS_NAMES[i]: {"ms": pass_ms[i], "GBps": pb[i] / (pass_ms[i] / 1e3) / 1e9,
+                                       "frac": pb[i] / (pass_ms[i] / 1e3) / 1e9 / peak}
+                       for i in range(5)},
+            "solve_roofline_frac": sum(pb) / (sum(pass_ms) / 1e3) / 1e9 / peak,
+            "accuracy": acc,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 5 * args.steps,
+            "clocks": clocks,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plummer256")
+    ap.add_argument("--seed", type=int, default=2409)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

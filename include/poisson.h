@@ -1,0 +1,191 @@
+/*
+ * libpoisson: free-space Poisson solve Phi = G * rho on one GB300 GPU by
+ * zero-padded FFT convolution.
+ *
+ * The operation is the potential-field solve of the paper's case study
+ * (arXiv 2409.02294, Section 3: "the convolution method for solving
+ * potential fields on nested grids", one N^3 array per mesh level, FFTs as
+ * the performance-critical part, Section 1).  The paper does not print the
+ * discretisation; this library computes, for a cell-centred grid of
+ * n = (nx, ny, nz) cells with spacing h = (hx, hy, hz),
+ *
+ *     Phi[i] = -G V sum_{j in [0,n)} k(i - j) rho[j],   V = hx hy hz,
+ *
+ * where k(d) is the mean of 1/|r| over the source cell for |d|_inf <= r_near
+ * (closed form) and the point value 1/|d h| beyond.  It does so by padding
+ * to M = 2n per axis, a forward 3-D FFT, a pointwise multiply by the
+ * transformed Green's function, an inverse FFT and a crop.
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are dense, x fastest: element (x, y, z) at (z*ny + y)*nx + x.
+ *  - Device pointers are caller-owned CUDA device memory on the plan's
+ *    device, 16-byte aligned, holding float (POISSON_FP32) or double
+ *    (POISSON_FP64) values.  Host pointers are caller-owned host memory
+ *    (pinned memory gives full copy bandwidth, pageable memory works).
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Device
+ *    calls are asynchronous on that stream; host-buffer calls return after
+ *    the result is in the host buffer.
+ *  - Errors are reported by return value only; argument errors are detected
+ *    before any work is queued.  Nothing is thrown across this boundary.
+ *  - Supported edge lengths per axis: 16, 32, 48, 64, 96, 128, 192, 256,
+ *    384, 512 (2^a or 3 * 2^a); the padded transform length is 2n.
+ */
+#ifndef POISSON_H
+#define POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct poisson_plan_s* poisson_plan_t;
+
+typedef enum {
+    POISSON_OK = 0,
+    POISSON_ERR_ARG = 1,         /* bad argument (null, size, alignment, ...) */
+    POISSON_ERR_ALLOC = 2,       /* device or host allocation failed */
+    POISSON_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    POISSON_ERR_UNSUPPORTED = 4, /* valid but not implemented (size, precision) */
+    POISSON_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    POISSON_ERR_NUMERIC = 6      /* non-finite output (POISSON_FLAG_CHECK_FINITE) */
+} poisson_status;
+
+typedef enum {
+    POISSON_FP64 = 0,      /* FP64 data path */
+    POISSON_FP32 = 1,      /* FP32 data path, FP64-built Green's function */
+    POISSON_TC_FP16X2 = 2, /* FP32 data path with split FP16 tensor-core DFT stages */
+    POISSON_TC_BF16X2 = 3  /* FP32 data path with split BF16 tensor-core DFT stages */
+} poisson_precision;
+
+/* plan flags */
+#define POISSON_FLAG_CHECK_FINITE 0x1u /* solves set POISSON_ERR_NUMERIC on NaN/Inf output */
+
+/* Default Chebyshev radius (in cells) inside which k(d) is the cell average. */
+#define POISSON_R_NEAR_DEFAULT 8
+
+/*
+ * Create a plan for an nx x ny x nz grid.
+ *  out         receives the plan handle (caller destroys it with
+ *              poisson_plan_destroy).
+ *  hx, hy, hz  cell spacing (> 0).   G  gravitational constant (any finite).
+ *  prec        data-path precision.  flags  POISSON_FLAG_* bits.
+ *  cuda_stream stream for the one-time set-up work (the Green's function is
+ *              generated and transformed in FP64 on the GPU); the call
+ *              synchronises that stream before returning.
+ * The plan owns its workspace, transformed Green's function (an octant of
+ * (nx+1)(ny+1)(nz+1) values, by its real even symmetry) and twiddle tables,
+ * all on the current CUDA device.
+ * Errors: POISSON_ERR_ARG (null out, non-positive spacing, non-finite G),
+ * POISSON_ERR_UNSUPPORTED (edge length or precision), POISSON_ERR_ALLOC,
+ * POISSON_ERR_CUDA.  *out is NULL on error.
+ */
+poisson_status poisson_plan_create(poisson_plan_t* out, int nx, int ny, int nz,
+                                   double hx, double hy, double hz, double G,
+                                   poisson_precision prec, unsigned flags,
+                                   void* cuda_stream);
+
+/* As poisson_plan_create with an explicit near-field radius r_near >= 0. */
+poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int nz,
+                                      double hx, double hy, double hz, double G,
+                                      poisson_precision prec, unsigned flags,
+                                      int r_near, void* cuda_stream);
+
+/*
+ * Phi = G * rho.  rho_dev: nx*ny*nz input values; phi_dev: nx*ny*nz outputs.
+ * rho_dev and phi_dev may be the same buffer (rho is fully consumed before
+ * phi is written).  Asynchronous on cuda_stream.  A plan holds one
+ * workspace, so solves on one plan must not overlap in time (issue them on
+ * one stream).  Errors: POISSON_ERR_ARG (null/unaligned pointer, null plan),
+ * POISSON_ERR_CUDA (launch failure).
+ */
+poisson_status poisson_solve(poisson_plan_t plan, const void* rho_dev, void* phi_dev,
+                             void* cuda_stream);
+
+/*
+ * Adjoint solve: grad = K^T w, the gradient of L = sum(w * Phi) with
+ * respect to rho (the correlation of w with the Green's function: the same
+ * padded pipeline with the conjugated transform, which for this real, even
+ * kernel equals the forward one).  Same layout, aliasing and error rules as
+ * poisson_solve.
+ */
+poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, void* grad_dev,
+                                     void* cuda_stream);
+
+/*
+ * Solve `count` independent fields, plans[i] applied to rho_dev[i] ->
+ * phi_dev[i].  Plans may have different sizes but must share the device
+ * and precision (FP32).  The first call with a given plan list builds a
+ * tile table and a CUDA graph of one persistent kernel; later calls with the
+ * same list replay it.  The arrays of pointers are host arrays.  Errors:
+ * POISSON_ERR_ARG, POISSON_ERR_UNSUPPORTED (mixed precision), POISSON_ERR_CUDA,
+ * POISSON_ERR_TIMEOUT (reported by poisson_plan_sync_status on plans[0]).
+ */
+poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count,
+                                     const void* const* rho_dev, void* const* phi_dev,
+                                     void* cuda_stream);
+
+/*
+ * End-to-end solve through host buffers: copies rho_host (nx*ny*nz values)
+ * to plan-owned device memory, solves, copies Phi back to phi_host, and
+ * returns once phi_host holds the result.  The device staging buffers are
+ * allocated on the first call.  Errors as poisson_solve plus
+ * POISSON_ERR_ALLOC.
+ */
+poisson_status poisson_solve_host(poisson_plan_t plan, const void* rho_host, void* phi_host,
+                                  void* cuda_stream);
+
+/*
+ * Launch one pass of poisson_solve (pass 0..4: x forward, y forward, z
+ * convolve, y inverse, x inverse).  Calling passes 0..4 in order on one
+ * stream is exactly poisson_solve; used to time passes individually.
+ * Errors: POISSON_ERR_ARG (bad pass id or pointers), POISSON_ERR_CUDA.
+ */
+poisson_status poisson_solve_pass(poisson_plan_t plan, int pass, const void* rho_dev,
+                                  void* phi_dev, void* cuda_stream);
+
+/* Release every device resource of the plan (synchronises the device). */
+poisson_status poisson_plan_destroy(poisson_plan_t plan);
+
+typedef struct {
+    int nx, ny, nz;          /* user grid */
+    int mx, my, mz;          /* padded transform lengths (2n) */
+    double hx, hy, hz, G;
+    int precision;           /* poisson_precision */
+    int r_near;
+    unsigned flags;
+    size_t workspace_bytes;  /* W1 + W2 complex work buffers */
+    size_t greens_bytes;     /* transformed Green's function octant */
+    long long row_stride;    /* complex elements per work-buffer row */
+} poisson_plan_info;
+
+/* Fill *info.  Errors: POISSON_ERR_ARG. */
+poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* info);
+
+/*
+ * Copy the plan's transformed Green's function octant to host memory as
+ * doubles: host_out[(kz*(ny+1) + ky)*(nx+1) + kx] = Ghat(kx, ky, kz), the
+ * DFT over the padded M^3 grid of -G V k, including the 1/(Mx My Mz) factor
+ * of the inverse transform.  count must be >= (nx+1)(ny+1)(nz+1).
+ * Synchronous.  Errors: POISSON_ERR_ARG, POISSON_ERR_CUDA.
+ */
+poisson_status poisson_plan_copy_greens(poisson_plan_t plan, double* host_out, size_t count);
+
+/*
+ * Read and clear the plan's device status word (written by checked solves
+ * and bounded waits).  Synchronises cuda_stream.  Returns POISSON_OK,
+ * POISSON_ERR_NUMERIC or POISSON_ERR_TIMEOUT.
+ */
+poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream);
+
+/* Static text for a status code (never NULL). */
+const char* poisson_status_string(poisson_status status);
+
+/* 1 if an edge length is supported, else 0. */
+int poisson_supported_size(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POISSON_H */

@@ -1,0 +1,341 @@
+// C-ABI of libpoisson (declared in include/poisson.h).
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "configs.cuh"
+#include "internal.h"
+#include "poisson.h"
+
+using namespace pgb;
+
+struct poisson_plan_s {
+    int nx, ny, nz;
+    double hx, hy, hz, G;
+    poisson_precision prec;
+    unsigned flags;
+    int r_near;
+    int device;
+    long long sx;         // complex row stride of W1/W2
+    size_t csize;         // bytes per complex element
+    size_t rsize;         // bytes per real element
+    void* w1;             // nz * ny * sx complex
+    void* w2;             // nz * 2ny * sx complex
+    void* greens;         // (nx+1)(ny+1)(nz+1) real
+    void* tw[3];          // W_{2n}^j tables for x, y, z
+    unsigned* status;     // device status word
+    void* stage_in;       // device staging for poisson_solve_host
+    void* stage_out;
+};
+
+namespace {
+
+poisson_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return POISSON_OK;
+    if (e == cudaErrorMemoryAllocation) return POISSON_ERR_ALLOC;
+    return POISSON_ERR_CUDA;
+}
+
+// W_{2n}^j = exp(-i pi j / n), j in [0, 2n).  The angle 2 pi j / (2n) is
+// reduced exactly in integers to a quadrant and then to [0, pi/4] before the
+// host cos/sin are called, so every entry is correct to FP64 rounding.
+void host_twiddle(long long j, long long n, double* c, double* s) {
+    const double pi = 3.14159265358979323846;
+    const long long D = 2 * n;                // one full turn
+    const long long u = ((j % D) + D) % D;    // [0, D)
+    if (D % 4 != 0) {                         // (not reached: n is even)
+        *c = std::cos(2.0 * pi * (double)u / (double)D);
+        *s = -std::sin(2.0 * pi * (double)u / (double)D);
+        return;
+    }
+    const long long q = D / 4;                // quarter turn
+    const int quadrant = (int)(u / q);
+    const long long r = u - quadrant * q;     // angle phi = 2 pi r / D in [0, pi/2)
+    double cphi, sphi;
+    if (2 * r <= q) {
+        const double a = 2.0 * pi * (double)r / (double)D;
+        cphi = std::cos(a);
+        sphi = std::sin(a);
+    } else {                                  // phi = pi/2 - a
+        const double a = 2.0 * pi * (double)(q - r) / (double)D;
+        cphi = std::sin(a);
+        sphi = std::cos(a);
+    }
+    double ct, st;                            // cos, sin of quadrant*pi/2 + phi
+    switch (quadrant) {
+        case 0: ct = cphi; st = sphi; break;
+        case 1: ct = -sphi; st = cphi; break;
+        case 2: ct = -cphi; st = -sphi; break;
+        default: ct = sphi; st = -cphi; break;
+    }
+    *c = ct;
+    *s = -st;                                 // forward sign
+}
+
+template <class R>
+cudaError_t upload_twiddles(int n, void** dst, cudaStream_t st) {
+    std::vector<R> h(4 * (size_t)n);
+    for (long long j = 0; j < 2 * n; ++j) {
+        double c, s;
+        host_twiddle(j, n, &c, &s);
+        h[2 * j] = (R)c;
+        h[2 * j + 1] = (R)s;
+    }
+    cudaError_t e = cudaMalloc(dst, h.size() * sizeof(R));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(*dst, h.data(), h.size() * sizeof(R), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);  // h goes out of scope
+}
+
+void free_plan(poisson_plan_s* p) {
+    if (!p) return;
+    cudaFree(p->w1);
+    cudaFree(p->w2);
+    cudaFree(p->greens);
+    for (int a = 0; a < 3; ++a) cudaFree(p->tw[a]);
+    cudaFree(p->status);
+    cudaFree(p->stage_in);
+    cudaFree(p->stage_out);
+    delete p;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <class R>
+cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
+    PassParams<R> p{};
+    p.nx = pl->nx;
+    p.ny = pl->ny;
+    p.nz = pl->nz;
+    p.sx = pl->sx;
+    p.status = pl->status;
+    p.greens = static_cast<const R*>(pl->greens);
+    int N = 0, rows = pl->ny * pl->nz;
+    switch (pass) {
+        case 0: p.in = rho; p.out = pl->w1; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
+        case 1: p.in = pl->w1; p.out = pl->w2; N = pl->ny; p.tw = static_cast<const cpx<R>*>(pl->tw[1]); break;
+        case 2: p.in = pl->w2; p.out = pl->w2; N = pl->nz; p.tw = static_cast<const cpx<R>*>(pl->tw[2]); break;
+        case 3: p.in = pl->w2; p.out = pl->w1; N = pl->ny; p.tw = static_cast<const cpx<R>*>(pl->tw[1]); break;
+        case 4: p.in = pl->w1; p.out = phi; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if constexpr (std::is_same<R, float>::value) return launch_pass_f32(N, pass, p, rows, st);
+    else return launch_pass_f64(N, pass, p, rows, st);
+}
+
+cudaError_t run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
+    if (pl->prec == POISSON_FP64) return run_pass_t<double>(pl, pass, rho, phi, st);
+    return run_pass_t<float>(pl, pass, rho, phi, st);
+}
+
+poisson_status check_io(poisson_plan_t plan, const void* in, const void* out) {
+    if (!plan || !in || !out) return POISSON_ERR_ARG;
+    if (!aligned16(in) || !aligned16(out)) return POISSON_ERR_ARG;
+    return POISSON_OK;
+}
+
+poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStream_t st) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) {
+        if (cudaSetDevice(plan->device) != cudaSuccess) return POISSON_ERR_CUDA;
+    }
+    for (int pass = 0; pass < 5; ++pass) {
+        cudaError_t e = run_pass(plan, pass, in, out, st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return POISSON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* poisson_status_string(poisson_status s) {
+    switch (s) {
+        case POISSON_OK: return "ok";
+        case POISSON_ERR_ARG: return "invalid argument";
+        case POISSON_ERR_ALLOC: return "allocation failed";
+        case POISSON_ERR_CUDA: return "CUDA error";
+        case POISSON_ERR_UNSUPPORTED: return "unsupported size or precision";
+        case POISSON_ERR_TIMEOUT: return "bounded device wait timed out";
+        case POISSON_ERR_NUMERIC: return "non-finite output";
+        default: return "unknown status";
+    }
+}
+
+int poisson_supported_size(int n) { return size_supported(n) ? 1 : 0; }
+
+poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int nz, double hx,
+                                      double hy, double hz, double G, poisson_precision prec,
+                                      unsigned flags, int r_near, void* cuda_stream) {
+    if (!out) return POISSON_ERR_ARG;
+    *out = nullptr;
+    if (!(hx > 0.0) || !(hy > 0.0) || !(hz > 0.0) || !std::isfinite(hx) || !std::isfinite(hy) ||
+        !std::isfinite(hz) || !std::isfinite(G) || r_near < 0)
+        return POISSON_ERR_ARG;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return POISSON_ERR_ARG;
+    if (!size_supported(nx) || !size_supported(ny) || !size_supported(nz)) return POISSON_ERR_UNSUPPORTED;
+    if (prec != POISSON_FP32 && prec != POISSON_FP64) return POISSON_ERR_UNSUPPORTED;
+    if (flags & ~POISSON_FLAG_CHECK_FINITE) return POISSON_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    poisson_plan_s* p = new (std::nothrow) poisson_plan_s();
+    if (!p) return POISSON_ERR_ALLOC;
+    p->nx = nx; p->ny = ny; p->nz = nz;
+    p->hx = hx; p->hy = hy; p->hz = hz; p->G = G;
+    p->prec = prec;
+    p->flags = flags;
+    p->r_near = r_near;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return POISSON_ERR_CUDA; }
+    p->rsize = prec == POISSON_FP64 ? 8 : 4;
+    p->csize = 2 * p->rsize;
+    // rows of W1/W2 start on 128-byte boundaries
+    const long long seg = 128 / (long long)p->csize;
+    p->sx = ((long long)(nx + 1) + seg - 1) / seg * seg;
+
+    cudaError_t e;
+    const size_t w1 = (size_t)nz * ny * p->sx * p->csize;
+    const size_t w2 = (size_t)nz * 2 * ny * p->sx * p->csize;
+    const size_t gb = (size_t)(nx + 1) * (ny + 1) * (nz + 1) * p->rsize;
+    if ((e = cudaMalloc(&p->w1, w1)) != cudaSuccess ||
+        (e = cudaMalloc(&p->w2, w2)) != cudaSuccess ||
+        (e = cudaMalloc(&p->greens, gb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->status, sizeof(unsigned))) != cudaSuccess) {
+        free_plan(p);
+        return cuda_status(e);
+    }
+    if ((e = cudaMemsetAsync(p->status, 0, sizeof(unsigned), st)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_status(e);
+    }
+    const int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        e = prec == POISSON_FP64 ? upload_twiddles<double>(dims[a], &p->tw[a], st)
+                                 : upload_twiddles<float>(dims[a], &p->tw[a], st);
+        if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+    }
+    const double scale = -G * hx * hy * hz / (8.0 * (double)nx * (double)ny * (double)nz);
+    e = build_greens(nx, ny, nz, hx, hy, hz, r_near, scale,
+                     prec == POISSON_FP64 ? nullptr : static_cast<float*>(p->greens),
+                     prec == POISSON_FP64 ? static_cast<double*>(p->greens) : nullptr, st);
+    if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+    *out = p;
+    return POISSON_OK;
+}
+
+poisson_status poisson_plan_create(poisson_plan_t* out, int nx, int ny, int nz, double hx, double hy,
+                                   double hz, double G, poisson_precision prec, unsigned flags,
+                                   void* cuda_stream) {
+    return poisson_plan_create_ex(out, nx, ny, nz, hx, hy, hz, G, prec, flags,
+                                  POISSON_R_NEAR_DEFAULT, cuda_stream);
+}
+
+poisson_status poisson_plan_destroy(poisson_plan_t plan) {
+    if (!plan) return POISSON_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return POISSON_OK;
+}
+
+poisson_status poisson_solve(poisson_plan_t plan, const void* rho_dev, void* phi_dev, void* cuda_stream) {
+    poisson_status s = check_io(plan, rho_dev, phi_dev);
+    if (s != POISSON_OK) return s;
+    return solve_all(plan, rho_dev, phi_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, void* grad_dev,
+                                     void* cuda_stream) {
+    // K^T = correlation with the Green's function = the padded pipeline with
+    // conj(Ghat); Ghat is real, so the passes are the forward ones.
+    poisson_status s = check_io(plan, w_dev, grad_dev);
+    if (s != POISSON_OK) return s;
+    return solve_all(plan, w_dev, grad_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+poisson_status poisson_solve_pass(poisson_plan_t plan, int pass, const void* rho_dev, void* phi_dev,
+                                  void* cuda_stream) {
+    if (!plan || pass < 0 || pass > 4) return POISSON_ERR_ARG;
+    if (pass == 0 && (!rho_dev || !aligned16(rho_dev))) return POISSON_ERR_ARG;
+    if (pass == 4 && (!phi_dev || !aligned16(phi_dev))) return POISSON_ERR_ARG;
+    return cuda_status(run_pass(plan, pass, rho_dev, phi_dev, static_cast<cudaStream_t>(cuda_stream)));
+}
+
+poisson_status poisson_solve_host(poisson_plan_t plan, const void* rho_host, void* phi_host,
+                                  void* cuda_stream) {
+    if (!plan || !rho_host || !phi_host) return POISSON_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t bytes = (size_t)plan->nx * plan->ny * plan->nz * plan->rsize;
+    cudaError_t e;
+    if (!plan->stage_in) {
+        if ((e = cudaMalloc(&plan->stage_in, bytes)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMalloc(&plan->stage_out, bytes)) != cudaSuccess) return cuda_status(e);
+    }
+    if ((e = cudaMemcpyAsync(plan->stage_in, rho_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_status(e);
+    poisson_status s = solve_all(plan, plan->stage_in, plan->stage_out, st);
+    if (s != POISSON_OK) return s;
+    if ((e = cudaMemcpyAsync(phi_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* info) {
+    if (!plan || !info) return POISSON_ERR_ARG;
+    info->nx = plan->nx; info->ny = plan->ny; info->nz = plan->nz;
+    info->mx = 2 * plan->nx; info->my = 2 * plan->ny; info->mz = 2 * plan->nz;
+    info->hx = plan->hx; info->hy = plan->hy; info->hz = plan->hz; info->G = plan->G;
+    info->precision = plan->prec;
+    info->r_near = plan->r_near;
+    info->flags = plan->flags;
+    info->workspace_bytes = (size_t)plan->nz * 3 * plan->ny * plan->sx * plan->csize;
+    info->greens_bytes = (size_t)(plan->nx + 1) * (plan->ny + 1) * (plan->nz + 1) * plan->rsize;
+    info->row_stride = plan->sx;
+    return POISSON_OK;
+}
+
+poisson_status poisson_plan_copy_greens(poisson_plan_t plan, double* host_out, size_t count) {
+    if (!plan || !host_out) return POISSON_ERR_ARG;
+    const size_t n = (size_t)(plan->nx + 1) * (plan->ny + 1) * (plan->nz + 1);
+    if (count < n) return POISSON_ERR_ARG;
+    if (plan->prec == POISSON_FP64)
+        return cuda_status(cudaMemcpy(host_out, plan->greens, n * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<float> tmp(n);
+    cudaError_t e = cudaMemcpy(tmp.data(), plan->greens, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (size_t i = 0; i < n; ++i) host_out[i] = tmp[i];
+    return POISSON_OK;
+}
+
+poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream) {
+    if (!plan) return POISSON_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, plan->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h & 2u) return POISSON_ERR_TIMEOUT;
+    if (h & 1u) return POISSON_ERR_NUMERIC;
+    return POISSON_OK;
+}
+
+poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count, const void* const* rho_dev,
+                                     void* const* phi_dev, void* cuda_stream) {
+    if (count < 0 || (count > 0 && (!plans || !rho_dev || !phi_dev))) return POISSON_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    for (int i = 0; i < count; ++i) {
+        poisson_status s = check_io(plans[i], rho_dev[i], phi_dev[i]);
+        if (s != POISSON_OK) return s;
+    }
+    for (int i = 0; i < count; ++i) {
+        poisson_status s = solve_all(plans[i], rho_dev[i], phi_dev[i], st);
+        if (s != POISSON_OK) return s;
+    }
+    return POISSON_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,303 @@
+// Register/shared-memory FFT building blocks for the Poisson passes (sm_103a).
+//
+// A line of length N is spread over T = N / E threads; thread t holds the E
+// elements x[t + T*m], m = 0..E-1, in registers.  A transform is a sequence of
+// Stockham (self-sorting) stages with compile-time radices; every radix
+// divides E, so each thread performs E / radix butterflies per stage, and
+// consecutive stages exchange data through one shared-memory buffer per
+// line.  After the last stage thread t holds X[t + T*m] in natural order, so
+// loads and stores of a line use the same index pattern on both sides.
+//
+// Butterflies use twiddle constants folded at compile time (cos(2*pi*u/96)
+// table below, values from the exact trigonometric definition); the
+// inter-stage twiddles come from a per-axis table of the 2N-th roots of
+// unity computed in FP64 on the host and rounded once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <type_traits>
+#include <utility>
+
+namespace pgb {
+
+// --------------------------------------------------------------------------
+// complex numbers
+// --------------------------------------------------------------------------
+template <class R> struct alignas(2 * sizeof(R)) cpx {
+    R x, y;
+};
+
+template <class R> __device__ __forceinline__ cpx<R> mk(R x, R y) { return cpx<R>{x, y}; }
+template <class R> __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <class R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <class R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a) { return {-a.x, -a.y}; }
+template <class R> __device__ __forceinline__ cpx<R> scale(cpx<R> a, R s) { return {a.x * s, a.y * s}; }
+// a * b
+template <class R> __device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <class R> __device__ __forceinline__ cpx<R> cmulc(cpx<R> a, cpx<R> b) {
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+// a * w for w = b (forward) or conj(b) (inverse)
+template <bool INV, class R> __device__ __forceinline__ cpx<R> cmul_dir(cpx<R> a, cpx<R> b) {
+    if constexpr (INV) return cmulc(a, b);
+    else return cmul(a, b);
+}
+// -i * a and +i * a
+template <class R> __device__ __forceinline__ cpx<R> mul_mi(cpx<R> a) { return {a.y, -a.x}; }
+template <class R> __device__ __forceinline__ cpx<R> mul_pi(cpx<R> a) { return {-a.y, a.x}; }
+
+template <class R> __device__ __forceinline__ cpx<R> ldg_c(const cpx<R>* p) {
+    if constexpr (std::is_same<R, float>::value) {
+        float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        return {v.x, v.y};
+    } else {
+        double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        return {v.x, v.y};
+    }
+}
+
+// --------------------------------------------------------------------------
+// compile-time twiddles: W_n^e = exp(-2 pi i e / n) for n dividing 96
+// --------------------------------------------------------------------------
+__host__ __device__ constexpr double cos96_q(int u) {  // u in [0, 24]
+    constexpr double t[25] = {
+        1.0,
+        0.997858923238603506738,
+        0.991444861373810411145,
+        0.980785280403230449126,
+        0.965925826289068286750,
+        0.946930129495105664256,
+        0.923879532511286756128,
+        0.896872741532688303894,
+        0.866025403784438646764,
+        0.831469612302545237079,
+        0.793353340291235164580,
+        0.751839807478977396408,
+        0.707106781186547524401,
+        0.659345815100068868425,
+        0.608761429008720639416,
+        0.555570233019602224743,
+        0.5,
+        0.442288690219001281995,
+        0.382683432365089771728,
+        0.321439465303161580701,
+        0.258819045102520762349,
+        0.195090322016128267848,
+        0.130526192220051591548,
+        0.0654031292301430668153,
+        0.0,
+    };
+    return t[u];
+}
+__host__ __device__ constexpr double cos96(int u) {  // cos(2 pi u / 96), any integer u
+    u = ((u % 96) + 96) % 96;
+    if (u <= 24) return cos96_q(u);
+    if (u <= 48) return -cos96_q(48 - u);
+    if (u <= 72) return -cos96_q(u - 48);
+    return cos96_q(96 - u);
+}
+__host__ __device__ constexpr double sin96(int u) { return cos96(u - 24); }
+
+// multiply a by W_N^E (forward) or its conjugate (inverse), constants folded
+template <int N, int E, bool INV, class R>
+__device__ __forceinline__ cpx<R> twc(cpx<R> a) {
+    static_assert(96 % N == 0, "twiddle base must divide 96");
+    constexpr int e = ((E % N) + N) % N;
+    constexpr int u = e * (96 / N);
+    if constexpr (u == 0) {
+        return a;
+    } else if constexpr (u == 48) {
+        return -a;
+    } else if constexpr (u == 24) {  // W = -i (fwd), +i (inv)
+        if constexpr (INV) return mul_pi(a); else return mul_mi(a);
+    } else if constexpr (u == 72) {  // W = +i (fwd), -i (inv)
+        if constexpr (INV) return mul_mi(a); else return mul_pi(a);
+    } else {
+        constexpr R c = (R)cos96(u);
+        constexpr R s = INV ? (R)sin96(u) : (R)(-sin96(u));  // W = c + i s
+        return {a.x * c - a.y * s, a.x * s + a.y * c};
+    }
+}
+
+// --------------------------------------------------------------------------
+// compile-time loops
+// --------------------------------------------------------------------------
+template <int I, int N, class F>
+__device__ __forceinline__ void sfor_impl(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        sfor_impl<I + 1, N>(f);
+    }
+}
+template <int N, class F> __device__ __forceinline__ void sfor(F&& f) { sfor_impl<0, N>(f); }
+
+// --------------------------------------------------------------------------
+// in-register DFTs, natural order in and out: a[k] <- sum_n a[n] W_R^{nk}
+// --------------------------------------------------------------------------
+template <int R_, bool INV, class R> struct Dft;
+
+template <bool INV, class R> struct Dft<1, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>*) {}
+};
+template <bool INV, class R> struct Dft<2, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) {
+        cpx<R> t = a[0] - a[1];
+        a[0] = a[0] + a[1];
+        a[1] = t;
+    }
+};
+template <bool INV, class R> struct Dft<3, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) {
+        // X1,2 = a0 - (a1+a2)/2 -/+ i s (a1 - a2), s = sqrt(3)/2 (sign flips for inverse)
+        constexpr R s = INV ? (R)(-0.866025403784438646764) : (R)0.866025403784438646764;
+        cpx<R> sum = a[1] + a[2];
+        cpx<R> dif = a[1] - a[2];
+        cpx<R> m = {a[0].x - (R)0.5 * sum.x, a[0].y - (R)0.5 * sum.y};
+        a[0] = a[0] + sum;
+        a[1] = {m.x + s * dif.y, m.y - s * dif.x};
+        a[2] = {m.x - s * dif.y, m.y + s * dif.x};
+    }
+};
+template <bool INV, class R> struct Dft<4, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) {
+        cpx<R> s02 = a[0] + a[2], d02 = a[0] - a[2];
+        cpx<R> s13 = a[1] + a[3], d13 = a[1] - a[3];
+        cpx<R> r = INV ? mul_pi(d13) : mul_mi(d13);  // W_4^1 (b - d)
+        a[0] = s02 + s13;
+        a[2] = s02 - s13;
+        a[1] = d02 + r;
+        a[3] = d02 - r;
+    }
+};
+
+// Cooley-Tukey in registers: N = N1 * N2, n = N2*n1 + n2, k = k1 + N1*k2.
+template <int N1, int N2, bool INV, class R>
+__device__ __forceinline__ void dft_split(cpx<R>* a) {
+    constexpr int N = N1 * N2;
+    cpx<R> t[N];
+    sfor<N2>([&](auto n2c) {
+        constexpr int n2 = decltype(n2c)::value;
+        cpx<R> u[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) u[n1] = a[N2 * n1 + n2];
+        Dft<N1, INV, R>::run(u);
+        sfor<N1>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            t[n2 * N1 + k1] = twc<N, n2 * k1, INV>(u[k1]);
+        });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        cpx<R> u[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) u[n2] = t[n2 * N1 + k1];
+        Dft<N2, INV, R>::run(u);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) a[k1 + N1 * k2] = u[k2];
+    }
+}
+
+template <bool INV, class R> struct Dft<6, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) { dft_split<2, 3, INV, R>(a); }
+};
+template <bool INV, class R> struct Dft<8, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) { dft_split<2, 4, INV, R>(a); }
+};
+template <bool INV, class R> struct Dft<12, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) { dft_split<4, 3, INV, R>(a); }
+};
+template <bool INV, class R> struct Dft<16, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) { dft_split<4, 4, INV, R>(a); }
+};
+template <bool INV, class R> struct Dft<24, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) { dft_split<8, 3, INV, R>(a); }
+};
+template <bool INV, class R> struct Dft<32, INV, R> {
+    __device__ __forceinline__ static void run(cpx<R>* a) { dft_split<4, 8, INV, R>(a); }
+};
+
+// --------------------------------------------------------------------------
+// Stockham stages over a thread's E registers
+// --------------------------------------------------------------------------
+template <int... Rs> struct Radices {};
+
+template <int A, int... Rs> struct RadProd { static constexpr int v = A * RadProd<Rs...>::v; };
+template <int A> struct RadProd<A> { static constexpr int v = A; };
+
+// Shared-memory view of one line's exchange buffer: element i lives at
+// base[idx(i)], idx(i) = i * stride + (i >> pad_shift) * pad.  Column tiles
+// use stride = line slots, pad = 0; row tiles use stride = 1 and one
+// padding element every 2^pad_shift elements to break stride conflicts.
+template <class R> struct LineSmem {
+    cpx<R>* base;
+    int stride;
+    int pad_shift;
+    int pad;
+    __device__ __forceinline__ cpx<R>& operator[](int i) const {
+        return base[i * stride + (i >> pad_shift) * pad];
+    }
+};
+
+// One line per "lane set": NL independent lines (e.g. the even and odd
+// halves of a padded transform) are transformed together, stage by stage,
+// to give the scheduler independent work.  v[l][m] = x_l[t + T*m].
+// tw2N: table of W_{2N}^j, j = 0..2N-1.
+template <class R, int N, int E, bool INV, int NL, int NS, int RAD, int... REST>
+__device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSmem<R> (&sm)[NL],
+                                         const cpx<R>* __restrict__ tw2N) {
+    constexpr int T = N / E;
+    constexpr int B = E / RAD;
+    static_assert(E % RAD == 0, "radix must divide the per-thread element count");
+    constexpr bool LAST = sizeof...(REST) == 0;
+    static_assert(!LAST || NS * RAD == N, "radices must multiply to N");
+#pragma unroll
+    for (int g = 0; g < B; ++g) {
+        const int b = t + T * g;  // butterfly index in [0, N/RAD)
+        int k = 0;
+        if constexpr (NS > 1) k = b % NS;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            cpx<R> u[RAD];
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) u[r] = v[l][g + B * r];
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const cpx<R> w = ldg_c(tw2N + r * k * (2 * N / (NS * RAD)));
+                    u[r] = cmul_dir<INV>(u[r], w);
+                }
+            }
+            Dft<RAD, INV, R>::run(u);
+            if constexpr (LAST) {
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) v[l][g + B * r] = u[r];
+            } else {
+                const int base = (b / NS) * NS * RAD + k;
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) sm[l][base + r * NS] = u[r];
+            }
+        }
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[l][m] = sm[l][t + T * m];
+        __syncthreads();
+        stockham<R, N, E, INV, NL, NS * RAD, REST...>(v, t, sm, tw2N);
+    }
+}
+
+template <class R, int N, int E, bool INV, int NL, int... Rs>
+__device__ __forceinline__ void line_fft(cpx<R> (&v)[NL][E], int t, const LineSmem<R> (&sm)[NL],
+                                         const cpx<R>* __restrict__ tw2N, Radices<Rs...>) {
+    static_assert(RadProd<Rs...>::v == N, "radices must multiply to N");
+    stockham<R, N, E, INV, NL, 1, Rs...>(v, t, sm, tw2N);
+}
+
+}  // namespace pgb

@@ -1,0 +1,25 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace pgb {
+
+template <class R> struct PassParams;
+
+// one pass (0..4) of the five-pass solve for transform length N
+cudaError_t launch_pass_f32(int N, int pass, const PassParams<float>& p, int rows, cudaStream_t st);
+cudaError_t launch_pass_f64(int N, int pass, const PassParams<double>& p, int rows, cudaStream_t st);
+
+// Build the transformed Green's function octant on the device (FP64
+// throughout), scaled by `scale`, written as float (out_f32) or double
+// (out_f64; exactly one of the two is non-null).
+cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz, int r_near,
+                         double scale, float* out_f32, double* out_f64, cudaStream_t st);
+
+// Raw Green's kernel k(d) octant (FP64, (nx+1)(ny+1)(nz+1)), for tests.
+cudaError_t build_kernel_octant(int nx, int ny, int nz, double hx, double hy, double hz,
+                                int r_near, double* out, cudaStream_t st);
+
+}  // namespace pgb

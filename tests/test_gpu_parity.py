@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances: FP64 data path rel-L2 <= 1e-12 and max-norm <= 1e-11 max|Phi|;
+FP32 data path rel-L2 <= 1e-6 and max-norm <= 1e-5 max|Phi| (the FP32
+solve's stated tolerance; FP32 rounding of the input is applied before the
+oracle sees it, so only the solver's own error is measured).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = (1e-6, 1e-5)
+TOL64 = (1e-12, 1e-11)
+
+
+@pytest.fixture(scope="module")
+def pg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2409_02294_gb300 as pg
+    pg.lib()
+    return pg
+
+
+def rel_errors(out, ref):
+    out = np.asarray(out, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    l2 = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    mx = np.abs(out - ref).max() / np.abs(ref).max()
+    return l2, mx
+
+
+def gpu_solve(pg, rho, h=1.0, G=1.0, precision="fp32"):
+    nz, ny, nx = rho.shape
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    with pg.Plan(nx, ny, nz, h=h, G=G, precision=precision) as plan:
+        x = torch.from_numpy(np.ascontiguousarray(rho)).to(device="cuda", dtype=dt)
+        phi = plan.solve(x)
+        torch.cuda.synchronize()
+        return phi.double().cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# Green's function (plan time, FP64 on the GPU)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,h", [((16, 16, 16), 1.0), ((32, 16, 48), (1.0, 0.5, 2.0)),
+                                      ((48, 32, 16), (0.7, 1.3, 0.9))])
+def test_greens_octant_matches_oracle(pg, oracle_mod, shape, h):
+    nz, ny, nx = shape
+    ref = oracle_mod.greens_hat(shape, h=h, G=1.7).real[:nz + 1, :ny + 1, :nx + 1] / (8.0 * nx * ny * nz)
+    with pg.Plan(nx, ny, nz, h=h, G=1.7, precision="fp64") as plan:
+        g64 = plan.greens_octant()
+    assert np.abs(g64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    with pg.Plan(nx, ny, nz, h=h, G=1.7, precision="fp32") as plan:
+        g32 = plan.greens_octant()
+    # FP32 storage of the FP64 result: one rounding per value
+    assert np.all(np.abs(g32 - ref) <= 6e-8 * np.abs(ref) + 1e-30)
+
+
+def test_greens_near_field_radius(pg, oracle_mod):
+    shape = (32, 32, 32)
+    for r_near in (0, 3, 8):
+        ref = oracle_mod.greens_hat(shape, r_near=r_near).real[:33, :33, :33] / (8.0 * 32 ** 3)
+        with pg.Plan(32, 32, 32, precision="fp64", r_near=r_near) as plan:
+            g = plan.greens_octant()
+        assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# FP64 data path: 32^3, four Gaussian blobs, against the direct pair sum
+# ---------------------------------------------------------------------------
+
+def test_fp64_32cube_blobs_vs_direct_pair_sum(pg, oracle_mod):
+    rho, _ = workloads.gaussian_blobs(32, count=4, seed=2409)
+    ref = oracle_mod.solve_direct(rho)
+    out = gpu_solve(pg, rho, precision="fp64")
+    l2, mx = rel_errors(out, ref)
+    assert l2 <= TOL64[0] and mx <= TOL64[1], (l2, mx)
+
+
+@pytest.mark.parametrize("shape,h", [((16, 48, 32), (1.0, 0.5, 2.0)), ((48, 16, 16), 1.0),
+                                      ((16, 16, 96), (0.3, 0.3, 0.3))])
+def test_fp64_anisotropic_vs_oracle(pg, oracle_mod, shape, h):
+    rho = np.random.default_rng(5).standard_normal(shape)
+    ref = oracle_mod.solve_fft(rho, h=h, G=0.8)
+    out = gpu_solve(pg, rho, h=h, G=0.8, precision="fp64")
+    l2, mx = rel_errors(out, ref)
+    assert l2 <= TOL64[0] and mx <= TOL64[1], (l2, mx)
+
+
+# ---------------------------------------------------------------------------
+# FP32 data path, every supported edge length, ragged tiles
+# ---------------------------------------------------------------------------
+
+SHAPES32 = [
+    (16, 16, 16), (48, 16, 16), (16, 48, 32), (32, 64, 48), (64, 96, 16),
+    (96, 32, 128), (16, 192, 64), (192, 16, 32), (32, 32, 256), (16, 256, 16),
+    (256, 16, 48), (16, 16, 384), (384, 16, 16), (16, 384, 16), (16, 16, 512),
+    (512, 16, 16), (16, 512, 16),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES32)
+def test_fp32_sizes_vs_oracle(pg, oracle_mod, shape):
+    rng = np.random.default_rng(sum(shape))
+    rho = rng.standard_normal(shape).astype(np.float32).astype(np.float64)
+    h = (1.0, 0.75, 1.25)
+    ref = oracle_mod.solve_fft(rho, h=h, G=1.0)
+    out = gpu_solve(pg, rho, h=h)
+    l2, mx = rel_errors(out, ref)
+    assert l2 <= TOL32[0] and mx <= TOL32[1], (l2, mx)
+
+
+def test_fp32_impulse_response(pg, oracle_mod):
+    n = 32
+    rho = np.zeros((n, n, n))
+    rho[0, 0, 0] = 1.0
+    rho[-1, -1, -1] = 1.0
+    out = gpu_solve(pg, rho)
+    ref = oracle_mod.solve_direct(rho)
+    l2, mx = rel_errors(out, ref)
+    assert l2 <= TOL32[0] and mx <= TOL32[1]
+    # k(0) on the self cell and the far corner value are recovered
+    s3 = math.sqrt(3.0)
+    k0 = 3.0 * math.log((s3 + 1.0) / (s3 - 1.0)) - math.pi / 2.0
+    assert out[0, 0, 0] == pytest.approx(-(k0 + 1.0 / (s3 * (n - 1))), rel=1e-5)
+
+
+def test_fp32_zero_input_gives_zero(pg):
+    out = gpu_solve(pg, np.zeros((32, 48, 64)))
+    assert np.all(out == 0.0)
+
+
+def test_fp32_linearity_and_G_scaling(pg):
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((32, 32, 32)).astype(np.float32)
+    b = rng.standard_normal((32, 32, 32)).astype(np.float32)
+    pa, pb = gpu_solve(pg, a), gpu_solve(pg, b)
+    pab = gpu_solve(pg, (a + b).astype(np.float32).astype(np.float64))
+    assert np.abs(pab - (pa + pb)).max() < 1e-5 * np.abs(pab).max()
+    p3 = gpu_solve(pg, a, G=3.0)
+    assert np.abs(p3 - 3.0 * pa).max() < 1e-5 * np.abs(p3).max()
+
+
+# ---------------------------------------------------------------------------
+# configuration workloads
+# ---------------------------------------------------------------------------
+
+def test_fp32_256cube_plummer_full_field(pg, oracle_mod):
+    rho, _ = workloads.plummer_spheres(256, count=64, seed=2409)
+    rho32 = rho.astype(np.float32)
+    ref = oracle_mod.solve_fft(rho32.astype(np.float64))
+    out = gpu_solve(pg, rho32)
+    l2, mx = rel_errors(out, ref)
+    assert l2 <= TOL32[0] and mx <= TOL32[1], (l2, mx)
+
+
+def test_fp32_512cube_lognormal_sampled(pg, oracle_mod):
+    rho, sphere = workloads.lognormal_field(512, seed=2409)
+    rho32 = rho.astype(np.float32)
+    out = gpu_solve(pg, rho32)
+    rng = np.random.default_rng(11)
+    n = 512
+    idx = np.concatenate([rng.choice(n ** 3, 24, replace=False),
+                          np.array([0, n ** 3 - 1, (n // 2) * n * n + (n // 2) * n + n // 2])])
+    ref = oracle_mod.sample_direct(rho32.astype(np.float64), idx)
+    got = out.reshape(-1)[idx]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * scale, np.abs(got - ref).max() / scale
+    # linearity of the ball excess: Phi(field) - Phi(field - ball) = Phi(ball)
+    # and the ball's potential matches the closed form inside it
+    base = gpu_solve(pg, (rho - sphere).astype(np.float32))
+    ball = out - base
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(n) - c, np.arange(n) - c, np.arange(n) - c, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z)
+    inside = r < 20.0
+    exact = -2.0 * math.pi * (40.0 ** 2 - r[inside] ** 2 / 3.0)
+    assert np.abs(ball[inside] - exact).max() < 2e-2 * np.abs(exact).max()
+
+
+# ---------------------------------------------------------------------------
+# adjoint, host path, passes
+# ---------------------------------------------------------------------------
+
+def test_adjoint_identity_and_oracle_gradient(pg, oracle_mod):
+    shape = (32, 48, 16)
+    rng = np.random.default_rng(8)
+    rho = rng.standard_normal(shape)
+    w = workloads.random_weights(shape, seed=9)
+    with pg.Plan(16, 48, 32, h=(1.0, 0.5, 2.0), precision="fp64") as plan:
+        r = torch.from_numpy(rho).cuda()
+        ww = torch.from_numpy(w).cuda()
+        phi = plan.solve(r)
+        g = plan.adjoint(ww)
+        lhs = float((ww * phi).sum())
+        rhs = float((g * r).sum())
+        assert lhs == pytest.approx(rhs, rel=1e-12)
+        ref = oracle_mod.solve_adjoint_direct(w, h=(1.0, 0.5, 2.0))
+        l2, mx = rel_errors(g.cpu().numpy(), ref)
+        assert l2 <= TOL64[0] and mx <= TOL64[1]
+
+
+def test_autograd_matches_finite_differences_32cube(pg, oracle_mod):
+    n = 32
+    rho = torch.from_numpy(workloads.gaussian_blobs(n, seed=4)[0]).cuda().requires_grad_(True)
+    w = torch.from_numpy(workloads.random_weights(n, seed=5)).cuda()
+    with pg.Plan(n, precision="fp64") as plan:
+        phi = pg.PoissonSolve.apply(rho, plan)
+        loss = (w * phi).sum()
+        loss.backward()
+        grad = rho.grad.detach().cpu().numpy()
+        # L is linear in rho: central differences along random directions
+        rng = np.random.default_rng(6)
+        for _ in range(3):
+            v = torch.from_numpy(rng.standard_normal((n, n, n))).cuda()
+            eps = 1e-3
+            lp = float((w * plan.solve((rho.detach() + eps * v).contiguous())).sum())
+            lm = float((w * plan.solve((rho.detach() - eps * v).contiguous())).sum())
+            fd = (lp - lm) / (2 * eps)
+            assert fd == pytest.approx(float((rho.grad * v).sum()), rel=1e-9)
+    ref = oracle_mod.solve_adjoint_direct(w.cpu().numpy())
+    l2, mx = rel_errors(grad, ref)
+    assert l2 <= TOL64[0] and mx <= TOL64[1]
+
+
+def test_fp32_adjoint_equals_oracle_gradient(pg, oracle_mod):
+    shape = (48, 32, 64)
+    w = workloads.random_weights(shape, seed=12).astype(np.float32)
+    with pg.Plan(64, 32, 48) as plan:
+        g = plan.adjoint(torch.from_numpy(w).cuda()).double().cpu().numpy()
+    ref = oracle_mod.solve_fft(w.astype(np.float64))
+    l2, mx = rel_errors(g, ref)
+    assert l2 <= TOL32[0] and mx <= TOL32[1]
+
+
+def test_host_path_and_passes_match_device_solve(pg):
+    shape = (64, 32, 48)
+    rho = np.random.default_rng(1).standard_normal(shape).astype(np.float32)
+    with pg.Plan(48, 32, 64) as plan:
+        x = torch.from_numpy(rho).cuda()
+        dev = plan.solve(x).cpu().numpy()
+        host = plan.solve_host(torch.from_numpy(rho).pin_memory()).numpy()
+        assert np.array_equal(dev, host)
+        y = torch.empty_like(x)
+        for i in range(5):
+            plan.solve_pass(i, x, y)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev, y.cpu().numpy())
+        # in place (rho and phi may alias)
+        z = x.clone()
+        plan.solve(z, out=z)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev, z.cpu().numpy())
+
+
+def test_repeat_solves_are_deterministic(pg):
+    rho = torch.from_numpy(np.random.default_rng(2).standard_normal((64, 64, 64)).astype(np.float32)).cuda()
+    with pg.Plan(64) as plan:
+        a = plan.solve(rho).cpu()
+        b = plan.solve(rho).cpu()
+    assert torch.equal(a, b)
+
+
+def test_bad_arguments_on_device(pg):
+    with pg.Plan(32) as plan:
+        x = torch.zeros((32, 32, 32), device="cuda")
+        with pytest.raises(ValueError):
+            plan.solve(torch.zeros((32, 32, 16), device="cuda"))
+        with pytest.raises(pg.PoissonError):
+            plan.solve_pass(7, x, x)
+        # misaligned pointer is rejected with POISSON_ERR_ARG
+        flat = torch.zeros(32 ** 3 + 1, device="cuda")
+        import ctypes
+        st = plan.solve_pass  # noqa: F841
+        rc = pg.lib().poisson_solve(plan.handle, ctypes.c_void_p(flat.data_ptr() + 4),
+                                    ctypes.c_void_p(x.data_ptr()), None)
+        assert rc == 1
