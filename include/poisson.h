@@ -178,6 +178,37 @@ poisson_status poisson_plan_copy_greens(poisson_plan_t plan, double* host_out, s
  */
 poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream);
 
+/*
+ * Allocation-free solve for small FP32 grids, without a plan.  (The paper has
+ * no counterpart; this exists for callers of the library.)
+ *
+ * For callers that must not call cudaMalloc when they solve: code inside a
+ * framework whose caching allocator owns device memory, code with a fixed
+ * memory budget, or code that cannot take the device synchronisation that
+ * allocating and freeing may cause.  Instead of plan-owned buffers, this call
+ * uses one fixed 16 MiB device array built into the library (held on every
+ * GPU that loads the library until the process exits); it allocates nothing
+ * and calls no allocating routine.  The caller passes only the FP32 input
+ * rho_dev and output phi_dev (nx*ny*nz values each, 16-byte aligned device
+ * memory); spacing, G and the result are as for a FP32 plan with the default
+ * near-field radius.  The Green's function is rebuilt on every call.
+ *
+ * Limits: the grid's Green's function, tables and work buffers must fit the
+ * 16 MiB array (64^3, or 128 x 64 x 64, fit; 128^3 does not); larger grids
+ * return POISSON_ERR_ARG before any work is queued.  Unsupported edge lengths
+ * return POISSON_ERR_UNSUPPORTED.
+ * Set-up: the first call on each device looks up the array's device address;
+ * make that first call before any stream capture starts.
+ * Sharing: all calls on a device share the array and it keeps the last call's
+ * contents (nothing in it needs to start at zero).  Calls whose GPU work
+ * overlaps in time race on it: issue them on one stream or serialise them.
+ * Asynchronous on cuda_stream.  Errors: POISSON_ERR_ARG, POISSON_ERR_UNSUPPORTED,
+ * POISSON_ERR_CUDA.
+ */
+poisson_status poisson_solve_noalloc(int nx, int ny, int nz, double hx, double hy, double hz,
+                                     double G, const void* rho_dev, void* phi_dev,
+                                     void* cuda_stream);
+
 /* Static text for a status code (never NULL). */
 const char* poisson_status_string(poisson_status status);
 

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("poisson_plan_get_info", _I, [_P, ctypes.POINTER(PlanInfo)]),
     ("poisson_plan_copy_greens", _I, [_P, ctypes.POINTER(_D), ctypes.c_size_t]),
     ("poisson_plan_sync_status", _I, [_P, _P]),
+    ("poisson_solve_noalloc", _I, [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P]),
     ("poisson_status_string", ctypes.c_char_p, [_I]),
     ("poisson_supported_size", _I, [_I]),
 ]
@@ -230,6 +231,24 @@ def solve_batched(plans, rhos, phis, stream=None):
     op = PA(*[ctypes.c_void_p(o.data_ptr()) for o in phis])
     _check(lib().poisson_solve_batched(hp, n, rp, op, _stream_handle(stream)), "poisson_solve_batched")
     return phis
+
+
+def solve_noalloc(rho, h=1.0, G=1.0, out=None, stream=None):
+    """Plan-free FP32 solve that allocates no device memory inside the
+    library (poisson_solve_noalloc); for small grids only (16 MiB scratch)."""
+    torch = _torch()
+    if not (isinstance(rho, torch.Tensor) and rho.is_cuda and rho.dtype == torch.float32
+            and rho.is_contiguous() and rho.dim() == 3):
+        raise ValueError("expected a contiguous 3-D float32 CUDA tensor")
+    if np.isscalar(h):
+        h = (h, h, h)
+    nz, ny, nx = rho.shape
+    if out is None:
+        out = torch.empty_like(rho)
+    _check(lib().poisson_solve_noalloc(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]), float(G),
+                                       ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       _stream_handle(stream)), "poisson_solve_noalloc")
+    return out
 
 
 def _make_autograd():

@@ -242,3 +242,40 @@ cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz
 }
 
 }  // namespace pgb
+
+namespace pgb {
+
+// The DCT-I transform and scaling of build_greens on caller-provided device
+// buffers, with nothing allocated and nothing synchronised: kbuf holds the
+// k(d) octant on entry and is overwritten, tmp has the same size, cx/cy/cz
+// are the (n+1)^2 DCT-I matrices of the three axes, out receives the scaled
+// FP32 octant.  All work is queued on st.
+cudaError_t greens_transform_into(double* kbuf, double* tmp, const double* cx, const double* cy,
+                                  const double* cz, int nx, int ny, int nz, double scale,
+                                  float* out, cudaStream_t st) {
+    const int ex = nx + 1, ey = ny + 1, ez = nz + 1;
+    const long long total = (long long)ex * ey * ez;
+    GemmDesc g{};
+    g.A = kbuf; g.sAi = ex; g.sAl = 1;
+    g.B = cx; g.sBl = 1; g.sBj = ex;
+    g.D = tmp; g.sDi = ex; g.sDj = 1;
+    g.I = ey * ez; g.J = ex; g.L = ex;
+    PGB_TRY(dgemm(g, 1, st));
+    g = GemmDesc{};
+    g.A = cy; g.sAi = ey; g.sAl = 1;
+    g.B = tmp; g.sBb = (long long)ey * ex; g.sBl = ex; g.sBj = 1;
+    g.D = kbuf; g.sDb = (long long)ey * ex; g.sDi = ex; g.sDj = 1;
+    g.I = ey; g.J = ex; g.L = ey;
+    PGB_TRY(dgemm(g, ez, st));
+    g = GemmDesc{};
+    g.A = cz; g.sAi = ez; g.sAl = 1;
+    g.B = kbuf; g.sBl = (long long)ey * ex; g.sBj = 1;
+    g.D = tmp; g.sDi = (long long)ey * ex; g.sDj = 1;
+    g.I = ez; g.J = ey * ex; g.L = ez;
+    PGB_TRY(dgemm(g, 1, st));
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    k_scale_store<<<blocks, 256, 0, st>>>(tmp, total, scale, out, nullptr);
+    return cudaGetLastError();
+}
+
+}  // namespace pgb

@@ -22,4 +22,10 @@ cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz
 cudaError_t build_kernel_octant(int nx, int ny, int nz, double hx, double hy, double hz,
                                 int r_near, double* out, cudaStream_t st);
 
+// DCT-I transform + scaling of a k(d) octant on caller-provided buffers
+// (no allocation, no synchronisation); see greens.cu.
+cudaError_t greens_transform_into(double* kbuf, double* tmp, const double* cx, const double* cy,
+                                  const double* cz, int nx, int ny, int nz, double scale,
+                                  float* out, cudaStream_t st);
+
 }  // namespace pgb
