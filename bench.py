@@ -223,7 +223,7 @@ def run_ours(args):
     rho32 = make_density(wl, args.seed + rank)
     rho = torch.from_numpy(rho32).to(dev)
     phi = torch.empty_like(rho)
-    plan = pg.Plan(n, n, n, precision="fp32")
+    plan = pg.Plan(n, n, n, precision="fp32", flags=pg.abi.FLAG_AUTOTUNE)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -332,6 +332,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 5 * args.steps,
+            "kernel_variants": plan.info()["variant"],
             "clocks": clocks,
             "wall_s_timed": t_wall,
         }

@@ -60,6 +60,7 @@ typedef enum {
 
 /* plan flags */
 #define POISSON_FLAG_CHECK_FINITE 0x1u /* solves set POISSON_ERR_NUMERIC on NaN/Inf output */
+#define POISSON_FLAG_AUTOTUNE 0x2u     /* run poisson_plan_autotune inside plan creation */
 
 /* Default Chebyshev radius (in cells) inside which k(d) is the cell average. */
 #define POISSON_R_NEAR_DEFAULT 8
@@ -157,10 +158,27 @@ typedef struct {
     size_t workspace_bytes;  /* W1 + W2 complex work buffers */
     size_t greens_bytes;     /* transformed Green's function octant */
     long long row_stride;    /* complex elements per work-buffer row */
+    int variant[5];          /* kernel variant in use per pass */
+    int variant_count[5];    /* variants available per pass */
 } poisson_plan_info;
 
 /* Fill *info.  Errors: POISSON_ERR_ARG. */
 poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* info);
+
+/*
+ * Autotuner: for each of the five passes, time every compiled kernel variant
+ * (lines per thread, CTA shape) on the plan's own buffers (one warm-up and
+ * three timed launches each, CUDA events on cuda_stream) and keep the
+ * fastest.  Results are bit-identical across variants of a pass only up to
+ * FP rounding order, which the variants share.  Synchronises cuda_stream;
+ * allocates two temporary grid-sized buffers.  Errors: POISSON_ERR_ARG,
+ * POISSON_ERR_ALLOC, POISSON_ERR_CUDA.
+ */
+poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream);
+
+/* Select kernel variant `variant` for `pass` (0..4) explicitly (for tests
+ * and experiments).  Errors: POISSON_ERR_ARG (out of range). */
+poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant);
 
 /*
  * Copy the plan's transformed Green's function octant to host memory as

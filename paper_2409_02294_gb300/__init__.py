@@ -14,6 +14,7 @@ Public entry points mirror the C-ABI of ``include/poisson.h``:
 * ``solve_batched(plans, rhos, phis)`` - ``poisson_solve_batched``
 * ``PoissonSolve`` - torch.autograd.Function (forward solve, backward adjoint)
 """
+from . import abi  # noqa: F401
 from .abi import (  # noqa: F401
     Plan,
     PoissonError,

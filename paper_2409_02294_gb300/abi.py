@@ -17,6 +17,7 @@ STATUS_NAMES = {
 }
 PRECISIONS = {"fp64": 0, "fp32": 1, "tc_fp16x2": 2, "tc_bf16x2": 3}
 FLAG_CHECK_FINITE = 0x1
+FLAG_AUTOTUNE = 0x2
 
 
 class PoissonError(RuntimeError):
@@ -34,6 +35,7 @@ class PlanInfo(ctypes.Structure):
         ("precision", ctypes.c_int), ("r_near", ctypes.c_int), ("flags", ctypes.c_uint),
         ("workspace_bytes", ctypes.c_size_t), ("greens_bytes", ctypes.c_size_t),
         ("row_stride", ctypes.c_longlong),
+        ("variant", ctypes.c_int * 5), ("variant_count", ctypes.c_int * 5),
     ]
 
 
@@ -52,6 +54,8 @@ SIGNATURES = [
     ("poisson_solve_pass", _I, [_P, _I, _P, _P, _P]),
     ("poisson_plan_destroy", _I, [_P]),
     ("poisson_plan_get_info", _I, [_P, ctypes.POINTER(PlanInfo)]),
+    ("poisson_plan_autotune", _I, [_P, _P]),
+    ("poisson_plan_set_variant", _I, [_P, _I, _I]),
     ("poisson_plan_copy_greens", _I, [_P, ctypes.POINTER(_D), ctypes.c_size_t]),
     ("poisson_plan_sync_status", _I, [_P, _P]),
     ("poisson_solve_noalloc", _I, [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P]),
@@ -141,7 +145,18 @@ class Plan:
     def info(self):
         inf = PlanInfo()
         _check(lib().poisson_plan_get_info(self.handle, ctypes.byref(inf)), "poisson_plan_get_info")
-        return {f: getattr(inf, f) for f, _ in PlanInfo._fields_}
+        out = {f: getattr(inf, f) for f, _ in PlanInfo._fields_}
+        out["variant"] = list(inf.variant)
+        out["variant_count"] = list(inf.variant_count)
+        return out
+
+    def autotune(self, stream=None):
+        _check(lib().poisson_plan_autotune(self.handle, _stream_handle(stream)), "poisson_plan_autotune")
+        return self.info()["variant"]
+
+    def set_variant(self, pass_id, variant):
+        _check(lib().poisson_plan_set_variant(self.handle, int(pass_id), int(variant)),
+               "poisson_plan_set_variant")
 
     # -- solves -------------------------------------------------------------
     def _io(self, x, out):

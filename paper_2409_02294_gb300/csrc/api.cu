@@ -29,6 +29,7 @@ struct poisson_plan_s {
     unsigned* status;     // device status word
     void* stage_in;       // device staging for poisson_solve_host
     void* stage_out;
+    int var[5];           // kernel variant per pass (autotuned or default)
 };
 
 namespace {
@@ -123,13 +124,64 @@ cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void
         case 4: p.in = pl->w1; p.out = phi; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
         default: return cudaErrorInvalidValue;
     }
-    if constexpr (std::is_same<R, float>::value) return launch_pass_f32(N, pass, p, rows, st);
-    else return launch_pass_f64(N, pass, p, rows, st);
+    if constexpr (std::is_same<R, float>::value) return launch_pass_f32(N, pass, pl->var[pass], p, rows, st);
+    else return launch_pass_f64(N, pass, pl->var[pass], p, rows, st);
 }
 
 cudaError_t run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
     if (pl->prec == POISSON_FP64) return run_pass_t<double>(pl, pass, rho, phi, st);
     return run_pass_t<float>(pl, pass, rho, phi, st);
+}
+
+// Default variant per pass before (or without) autotuning.
+int default_variant(poisson_precision prec, int pass) {
+    if (prec == POISSON_FP64) return 0;
+    return (pass == 0 || pass == 4) ? 0 : 1;
+}
+
+// Time every variant of every pass on the plan's own buffers and keep the
+// fastest (minimum of 3 timed launches after one warm-up launch each).
+poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
+    const size_t cells = (size_t)pl->nx * pl->ny * pl->nz;
+    void *rho = nullptr, *phi = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    const size_t w1 = (size_t)pl->nz * pl->ny * pl->sx * pl->csize;
+    do {
+        if ((e = cudaMalloc(&rho, cells * pl->rsize))) break;
+        if ((e = cudaMalloc(&phi, cells * pl->rsize))) break;
+        if ((e = cudaMemsetAsync(rho, 0, cells * pl->rsize, st))) break;
+        if ((e = cudaMemsetAsync(pl->w1, 0, w1, st))) break;
+        if ((e = cudaMemsetAsync(pl->w2, 0, 2 * w1, st))) break;
+        if ((e = cudaEventCreate(&e0))) break;
+        if ((e = cudaEventCreate(&e1))) break;
+        for (int pass = 0; pass < 5 && e == cudaSuccess; ++pass) {
+            const int nv = pass_variants(pl->prec == POISSON_FP64, pass);
+            float best = 1e30f;
+            int best_v = pl->var[pass];
+            for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+                pl->var[pass] = v;
+                if ((e = run_pass(pl, pass, rho, phi, st))) break;
+                float tmin = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    if ((e = cudaEventRecord(e0, st))) break;
+                    if ((e = run_pass(pl, pass, rho, phi, st))) break;
+                    if ((e = cudaEventRecord(e1, st))) break;
+                    if ((e = cudaEventSynchronize(e1))) break;
+                    float ms = 0.f;
+                    if ((e = cudaEventElapsedTime(&ms, e0, e1))) break;
+                    tmin = ms < tmin ? ms : tmin;
+                }
+                if (tmin < best) { best = tmin; best_v = v; }
+            }
+            pl->var[pass] = best_v;
+        }
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(rho);
+    cudaFree(phi);
+    return cuda_status(e);
 }
 
 poisson_status check_io(poisson_plan_t plan, const void* in, const void* out) {
@@ -180,7 +232,7 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
     if (nx <= 0 || ny <= 0 || nz <= 0) return POISSON_ERR_ARG;
     if (!size_supported(nx) || !size_supported(ny) || !size_supported(nz)) return POISSON_ERR_UNSUPPORTED;
     if (prec != POISSON_FP32 && prec != POISSON_FP64) return POISSON_ERR_UNSUPPORTED;
-    if (flags & ~POISSON_FLAG_CHECK_FINITE) return POISSON_ERR_ARG;
+    if (flags & ~(POISSON_FLAG_CHECK_FINITE | POISSON_FLAG_AUTOTUNE)) return POISSON_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
     poisson_plan_s* p = new (std::nothrow) poisson_plan_s();
@@ -190,6 +242,7 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
     p->prec = prec;
     p->flags = flags;
     p->r_near = r_near;
+    for (int pass = 0; pass < 5; ++pass) p->var[pass] = default_variant(prec, pass);
     if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return POISSON_ERR_CUDA; }
     p->rsize = prec == POISSON_FP64 ? 8 : 4;
     p->csize = 2 * p->rsize;
@@ -223,6 +276,10 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
                      prec == POISSON_FP64 ? nullptr : static_cast<float*>(p->greens),
                      prec == POISSON_FP64 ? static_cast<double*>(p->greens) : nullptr, st);
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+    if (flags & POISSON_FLAG_AUTOTUNE) {
+        poisson_status s = autotune(p, st);
+        if (s != POISSON_OK) { free_plan(p); return s; }
+    }
     *out = p;
     return POISSON_OK;
 }
@@ -294,6 +351,22 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
     info->workspace_bytes = (size_t)plan->nz * 3 * plan->ny * plan->sx * plan->csize;
     info->greens_bytes = (size_t)(plan->nx + 1) * (plan->ny + 1) * (plan->nz + 1) * plan->rsize;
     info->row_stride = plan->sx;
+    for (int pass = 0; pass < 5; ++pass) {
+        info->variant[pass] = plan->var[pass];
+        info->variant_count[pass] = pass_variants(plan->prec == POISSON_FP64, pass);
+    }
+    return POISSON_OK;
+}
+
+poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream) {
+    if (!plan) return POISSON_ERR_ARG;
+    return autotune(plan, static_cast<cudaStream_t>(cuda_stream));
+}
+
+poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant) {
+    if (!plan || pass < 0 || pass > 4) return POISSON_ERR_ARG;
+    if (variant < 0 || variant >= pass_variants(plan->prec == POISSON_FP64, pass)) return POISSON_ERR_ARG;
+    plan->var[pass] = variant;
     return POISSON_OK;
 }
 

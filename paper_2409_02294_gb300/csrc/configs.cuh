@@ -2,14 +2,15 @@
 // Stockham radix sequence.  Every radix divides E; radices multiply to N.
 #pragma once
 
+#include <tuple>
+
 #include "passes.cuh"
 
 namespace pgb {
 
 template <class R, int N> struct SizeCfg;
 
-// FP32: E up to 24 complex values per line, two lines (even/odd halves) per
-// thread.
+// FP32: E up to 32 complex values per thread (one line per thread).
 template <> struct SizeCfg<float, 16>  { using C = LineCfg<float, 16, 16, Radices<16>>; };
 template <> struct SizeCfg<float, 32>  { using C = LineCfg<float, 32, 8, Radices<8, 4>>; };
 template <> struct SizeCfg<float, 48>  { using C = LineCfg<float, 48, 12, Radices<12, 4>>; };
@@ -19,7 +20,7 @@ template <> struct SizeCfg<float, 128> { using C = LineCfg<float, 128, 16, Radic
 template <> struct SizeCfg<float, 192> { using C = LineCfg<float, 192, 24, Radices<24, 8>>; };
 template <> struct SizeCfg<float, 256> { using C = LineCfg<float, 256, 16, Radices<16, 16>>; };
 template <> struct SizeCfg<float, 384> { using C = LineCfg<float, 384, 24, Radices<24, 8, 2>>; };
-template <> struct SizeCfg<float, 512> { using C = LineCfg<float, 512, 16, Radices<16, 16, 2>>; };
+template <> struct SizeCfg<float, 512> { using C = LineCfg<float, 512, 32, Radices<32, 16>>; };
 
 // FP64: smaller E (twice the registers per value).
 template <> struct SizeCfg<double, 16>  { using C = LineCfg<double, 16, 8, Radices<8, 2>>; };
@@ -31,7 +32,7 @@ template <> struct SizeCfg<double, 128> { using C = LineCfg<double, 128, 8, Radi
 template <> struct SizeCfg<double, 192> { using C = LineCfg<double, 192, 12, Radices<12, 4, 4>>; };
 template <> struct SizeCfg<double, 256> { using C = LineCfg<double, 256, 8, Radices<8, 8, 4>>; };
 template <> struct SizeCfg<double, 384> { using C = LineCfg<double, 384, 12, Radices<12, 4, 4, 2>>; };
-template <> struct SizeCfg<double, 512> { using C = LineCfg<double, 512, 8, Radices<8, 8, 8>>; };
+template <> struct SizeCfg<double, 512> { using C = LineCfg<double, 512, 16, Radices<16, 16, 2>>; };
 
 inline bool size_supported(int n) {
     switch (n) {
@@ -41,27 +42,69 @@ inline bool size_supported(int n) {
     }
 }
 
-// Dispatch one pass for edge length N (the pass's transform axis).
-template <class R, int N>
-cudaError_t launch_pass_n(int pass, const PassParams<R>& p, int rows, cudaStream_t st) {
-    using C = typename SizeCfg<R, N>::C;
-    if (pass == 0 || pass == 4) return launch_row<C>(pass, p, rows, st);
-    return launch_col<C>(pass, p, st);
+// Variants the autotuner chooses from (per pass and edge length).
+//   column passes (y forward, z convolve, y inverse): lines per thread and
+//   CTA threads; row passes (x forward, x inverse) likewise.
+template <class R> struct Variants;
+template <> struct Variants<float> {
+    using Col = std::tuple<Var<2, 128>, Var<2, 256>, Var<1, 256>, Var<1, 512>>;
+    using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>>;
+};
+template <> struct Variants<double> {
+    using Col = std::tuple<Var<1, 256>>;
+    using Row = std::tuple<Var<1, 256>>;
+};
+template <class R> constexpr int num_variants(int pass) {
+    return (pass == 0 || pass == 4) ? (int)std::tuple_size<typename Variants<R>::Row>::value
+                                    : (int)std::tuple_size<typename Variants<R>::Col>::value;
 }
 
-template <class R>
-cudaError_t launch_pass_t(int N, int pass, const PassParams<R>& p, int rows, cudaStream_t st) {
+enum PassGroup { GROUP_ROW = 0, GROUP_Y = 1, GROUP_Z = 2 };
+inline int pass_group(int pass) { return (pass == 0 || pass == 4) ? GROUP_ROW : (pass == 2 ? GROUP_Z : GROUP_Y); }
+
+template <class C, class Tuple, int I = 0>
+cudaError_t launch_row_var(int var, int pass, const PassParams<typename C::R>& p, int rows, cudaStream_t st) {
+    if constexpr (I < (int)std::tuple_size<Tuple>::value) {
+        if (var == I) return launch_row<C, typename std::tuple_element<I, Tuple>::type>(pass, p, rows, st);
+        return launch_row_var<C, Tuple, I + 1>(var, pass, p, rows, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+template <class C, class Tuple, int I = 0>
+cudaError_t launch_col_var(int var, int pass, const PassParams<typename C::R>& p, cudaStream_t st) {
+    if constexpr (I < (int)std::tuple_size<Tuple>::value) {
+        if (var == I) return launch_col<C, typename std::tuple_element<I, Tuple>::type>(pass, p, st);
+        return launch_col_var<C, Tuple, I + 1>(var, pass, p, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Dispatch one pass of group GROUP for edge length N (the pass's axis).
+template <class R, int GROUP, int N>
+cudaError_t launch_group_n(int pass, int var, const PassParams<R>& p, int rows, cudaStream_t st) {
+    using C = typename SizeCfg<R, N>::C;
+    if constexpr (GROUP == GROUP_ROW) {
+        return launch_row_var<C, typename Variants<R>::Row>(var, pass, p, rows, st);
+    } else {
+        return launch_col_var<C, typename Variants<R>::Col>(var, pass, p, st);
+    }
+}
+
+template <class R, int GROUP>
+cudaError_t launch_group(int N, int pass, int var, const PassParams<R>& p, int rows, cudaStream_t st) {
     switch (N) {
-        case 16: return launch_pass_n<R, 16>(pass, p, rows, st);
-        case 32: return launch_pass_n<R, 32>(pass, p, rows, st);
-        case 48: return launch_pass_n<R, 48>(pass, p, rows, st);
-        case 64: return launch_pass_n<R, 64>(pass, p, rows, st);
-        case 96: return launch_pass_n<R, 96>(pass, p, rows, st);
-        case 128: return launch_pass_n<R, 128>(pass, p, rows, st);
-        case 192: return launch_pass_n<R, 192>(pass, p, rows, st);
-        case 256: return launch_pass_n<R, 256>(pass, p, rows, st);
-        case 384: return launch_pass_n<R, 384>(pass, p, rows, st);
-        case 512: return launch_pass_n<R, 512>(pass, p, rows, st);
+        case 16: return launch_group_n<R, GROUP, 16>(pass, var, p, rows, st);
+        case 32: return launch_group_n<R, GROUP, 32>(pass, var, p, rows, st);
+        case 48: return launch_group_n<R, GROUP, 48>(pass, var, p, rows, st);
+        case 64: return launch_group_n<R, GROUP, 64>(pass, var, p, rows, st);
+        case 96: return launch_group_n<R, GROUP, 96>(pass, var, p, rows, st);
+        case 128: return launch_group_n<R, GROUP, 128>(pass, var, p, rows, st);
+        case 192: return launch_group_n<R, GROUP, 192>(pass, var, p, rows, st);
+        case 256: return launch_group_n<R, GROUP, 256>(pass, var, p, rows, st);
+        case 384: return launch_group_n<R, GROUP, 384>(pass, var, p, rows, st);
+        case 512: return launch_group_n<R, GROUP, 512>(pass, var, p, rows, st);
         default: return cudaErrorInvalidValue;
     }
 }

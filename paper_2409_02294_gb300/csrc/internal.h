@@ -8,9 +8,15 @@ namespace pgb {
 
 template <class R> struct PassParams;
 
-// one pass (0..4) of the five-pass solve for transform length N
-cudaError_t launch_pass_f32(int N, int pass, const PassParams<float>& p, int rows, cudaStream_t st);
-cudaError_t launch_pass_f64(int N, int pass, const PassParams<double>& p, int rows, cudaStream_t st);
+// One pass (0..4) of the five-pass solve for transform length N, kernel
+// variant `var` (0 <= var < pass_variants(precision, pass)).
+cudaError_t launch_pass_f32(int N, int pass, int var, const PassParams<float>& p, int rows, cudaStream_t st);
+cudaError_t launch_pass_f64(int N, int pass, int var, const PassParams<double>& p, int rows, cudaStream_t st);
+int pass_variants(bool fp64, int pass);
+// per-group entry points (one translation unit each)
+cudaError_t launch_row_f32(int N, int pass, int var, const PassParams<float>& p, int rows, cudaStream_t st);
+cudaError_t launch_y_f32(int N, int pass, int var, const PassParams<float>& p, cudaStream_t st);
+cudaError_t launch_z_f32(int N, int pass, int var, const PassParams<float>& p, cudaStream_t st);
 
 // Build the transformed Green's function octant on the device (FP64
 // throughout), scaled by `scale`, written as float (out_f32) or double

@@ -190,7 +190,8 @@ extern "C" poisson_status poisson_solve_noalloc(int nx, int ny, int nz, double h
             case 3: p.in = w2; p.out = w1; N = ny; p.tw = reinterpret_cast<const cpx<float>*>(tw[1]); break;
             default: p.in = w1; p.out = phi_dev; N = nx; p.tw = reinterpret_cast<const cpx<float>*>(tw[0]); break;
         }
-        if ((e = launch_pass_f32(N, pass, p, ny * nz, st)) != cudaSuccess) return to_status(e);
+        if ((e = launch_pass_f32(N, pass, (pass == 0 || pass == 4) ? 0 : 1, p, ny * nz, st)) != cudaSuccess)
+            return to_status(e);
     }
     return POISSON_OK;
 }

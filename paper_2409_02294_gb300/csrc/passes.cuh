@@ -50,9 +50,8 @@ template <class R> struct Seg { static constexpr int XW = 128 / (int)sizeof(cpx<
 // Column passes (y and z axes; lines are strided, tiles span x)
 // ==========================================================================
 //
-// Thread layout: slot = tid % SLOTS (fastest), t = tid / SLOTS.  "Wide"
-// tiles map slot -> (kx = x0 + slot % XW, other = o0 + slot / XW), so 16
-// (FP32) or 8 (FP64) consecutive lanes read one 128-byte segment of a row.
+// Tiles: "wide" tiles map slot -> (kx = x0 + slot % XW, other = o0 + slot /
+// XW), so XW consecutive lanes read one row segment of up to 128 bytes.
 // Columns beyond the last full segment (the Nyquist column kx = nx when nx
 // is a multiple of XW) go to "narrow" tiles: slot -> other index.
 
@@ -64,7 +63,7 @@ template <class R, int SLOTS> struct ColTile {
 
 template <class R, int SLOTS>
 __device__ __forceinline__ ColTile<R, SLOTS> col_tile(int ncols, int L, int slot) {
-    constexpr int XW = Seg<R>::XW;
+    constexpr int XW = SLOTS < Seg<R>::XW ? SLOTS : Seg<R>::XW;
     constexpr int NLW = SLOTS / XW;
     const int nxw = ncols / XW;
     const int wide_l = (L + NLW - 1) / NLW;
@@ -88,143 +87,202 @@ __device__ __forceinline__ ColTile<R, SLOTS> col_tile(int ncols, int L, int slot
 
 template <class R, int SLOTS>
 inline int col_grid(int ncols, int L) {
-    constexpr int XW = Seg<R>::XW;
+    constexpr int XW = SLOTS < Seg<R>::XW ? SLOTS : Seg<R>::XW;
     constexpr int NLW = SLOTS / XW;
     const int nxw = ncols / XW;
     const int nleft = ncols - nxw * XW;
     return nxw * ((L + NLW - 1) / NLW) + nleft * ((L + SLOTS - 1) / SLOTS);
 }
 
+// Column kernels: thread = (slot, t[, q]) with slot fastest, then t (the
+// position within the line).  LPT = 2: a thread carries both halves of its
+// column (X[2k] and X[2k+1] of the padded transform); LPT = 1: the halves go
+// to two thread groups (q = tid / (SLOTS T)) that meet through shared memory
+// for the final combine.
+
+template <class Cfg, int SLOTS, int LPT> struct ColIds {
+    int slot, t, q;
+    __device__ __forceinline__ ColIds() {
+        slot = threadIdx.x % SLOTS;
+        const int rest = threadIdx.x / SLOTS;
+        t = rest % Cfg::T;
+        q = LPT == 1 ? rest / Cfg::T : 0;
+    }
+    // half carried in register line l
+    __device__ __forceinline__ int half(int l) const { return LPT == 2 ? l : q; }
+};
+
+template <class Cfg, int SLOTS, int LPT> constexpr int col_threads() {
+    return (LPT == 1 ? 2 : 1) * SLOTS * Cfg::T;
+}
+
 // pass 1: pad + forward FFT along y.  W1 -> W2.
-template <class Cfg, int SLOTS>
-__global__ void __launch_bounds__(SLOTS * Cfg::T)
+template <class Cfg, int SLOTS, int LPT>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>())
 k_y_fwd(PassParams<typename Cfg::R> p) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
-    const int slot = threadIdx.x % SLOTS, t = threadIdx.x / SLOTS;
-    const int ny = p.ny, nz = p.nz;
-    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, nz, slot);
+    const ColIds<Cfg, SLOTS, LPT> id;
+    const int ny = p.ny;
+    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, p.nz, id.slot);
     const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
     cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
     const long long sx = p.sx;
 
-    cpx<R> v[2][E];
-    const long long ibase = (long long)c.other * ny * sx + c.kx;
+    cpx<R> v[LPT][E];
+    const cpx<R>* src = in + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int j = t + T * m;
-        v[0][m] = c.valid ? in[ibase + (long long)j * sx] : cpx<R>{0, 0};
+    for (int m = 0; m < E; ++m) v[0][m] = c.valid ? src[(long long)(T * m) * sx] : cpx<R>{0, 0};
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+        if (id.half(l)) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + id.t + T * m));
+        }
     }
+    LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[1][m] = cmul(v[0][m], ldg_c(p.tw + t + T * m));
-
-    const LineSmem<R> ls[2] = {{sm + slot, SLOTS, 30, 0}, {sm + N * SLOTS + slot, SLOTS, 30, 0}};
-    line_fft<R, N, E, false, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + id.half(l) * N * SLOTS + id.slot, SLOTS, 30, 0};
+    line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
     if (c.valid) {
-        const long long obase = (long long)c.other * 2 * ny * sx + c.kx;
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int l = 0; l < LPT; ++l) {
+            cpx<R>* dst = out + (long long)c.other * 2 * ny * sx + c.kx +
+                          (long long)(id.half(l) * ny + id.t) * sx;
 #pragma unroll
-            for (int m = 0; m < E; ++m)
-                out[obase + (long long)(q * ny + t + T * m) * sx] = v[q][m];
+            for (int m = 0; m < E; ++m) dst[(long long)(T * m) * sx] = v[l][m];
+        }
+    }
+}
+
+// Final combine of the cropped inverse, x[j] = a[j] + W_2N^-j b[j] with a,b
+// the inverse transforms of the even and odd halves.  Returns true in the
+// threads that hold x[t + T m] in v[0][m] afterwards.
+template <class Cfg, int SLOTS, int LPT>
+__device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cfg::E],
+                                               const ColIds<Cfg, SLOTS, LPT>& id,
+                                               cpx<typename Cfg::R>* sm,
+                                               const cpx<typename Cfg::R>* tw) {
+    using R = typename Cfg::R;
+    constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
+    if constexpr (LPT == 2) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + cmulc(v[1][m], ldg_c(tw + id.t + T * m));
+        return true;
+    } else {
+        const LineSmem<R> lodd = {sm + N * SLOTS + id.slot, SLOTS, 30, 0};
+        if (id.q) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int j = id.t + T * m;
+                lodd[j] = cmulc(v[0][m], ldg_c(tw + j));
+            }
+        }
+        __syncthreads();
+        if (!id.q) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + lodd[id.t + T * m];
+        }
+        return id.q == 0;
     }
 }
 
 // pass 2: pad + FFT along z, multiply by Ghat, inverse FFT along z, crop.
 // In place on W2.  Ghat is real (the kernel is real and even), so the
 // adjoint's conj(Ghat) is the same multiply.
-template <class Cfg, int SLOTS>
-__global__ void __launch_bounds__(SLOTS * Cfg::T)
+template <class Cfg, int SLOTS, int LPT>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>())
 k_z_conv(PassParams<typename Cfg::R> p) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
-    const int slot = threadIdx.x % SLOTS, t = threadIdx.x / SLOTS;
+    const ColIds<Cfg, SLOTS, LPT> id;
     const int nx = p.nx, ny = p.ny;
-    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(nx + 1, 2 * ny, slot);
+    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(nx + 1, 2 * ny, id.slot);
     cpx<R>* __restrict__ w = static_cast<cpx<R>*>(p.out);
-    const long long sx = p.sx;
-    const long long plane = 2LL * ny * sx;
+    const long long plane = 2LL * ny * p.sx;
 
-    cpx<R> v[2][E];
-    const long long base = (long long)c.other * sx + c.kx;
+    cpx<R> v[LPT][E];
+    cpx<R>* col = w + (long long)c.other * p.sx + c.kx;
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int j = t + T * m;
-        v[0][m] = c.valid ? w[base + (long long)j * plane] : cpx<R>{0, 0};
+    for (int m = 0; m < E; ++m)
+        v[0][m] = c.valid ? col[(long long)(id.t + T * m) * plane] : cpx<R>{0, 0};
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+        if (id.half(l)) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + id.t + T * m));
+        }
     }
+    LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[1][m] = cmul(v[0][m], ldg_c(p.tw + t + T * m));
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + id.half(l) * N * SLOTS + id.slot, SLOTS, 30, 0};
+    line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
-    const LineSmem<R> ls[2] = {{sm + slot, SLOTS, 30, 0}, {sm + N * SLOTS + slot, SLOTS, 30, 0}};
-    line_fft<R, N, E, false, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
-
-    // Green's multiply: frequency (kx, ky, kz), folded into the octant.
-    {
+    // Green's multiply at frequency (kx, ky, kz), folded into the octant.
+    // kz = 2 (t + T m) + q is <= N exactly for m < E/2.
+    if (c.valid) {
         const int kys = c.other;
         const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
         const int kyf = ky <= ny ? ky : 2 * ny - ky;
-        const R* __restrict__ g = p.greens + (long long)kyf * (nx + 1) + c.kx;
         const long long gz = (long long)(ny + 1) * (nx + 1);
+        const R* __restrict__ g = p.greens + (long long)kyf * (nx + 1) + c.kx;
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int l = 0; l < LPT; ++l) {
+            const int kz0 = 2 * id.t + id.half(l);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                const int kz = 2 * (t + T * m) + q;
-                const int kzf = kz <= N ? kz : 2 * N - kz;
-                const R gv = c.valid ? __ldg(g + kzf * gz) : (R)0;
-                v[q][m] = scale(v[q][m], gv);
+                const int kz = kz0 + 2 * T * m;
+                const int kzf = (m < E / 2) ? kz : 2 * N - kz;
+                v[l][m] = scale(v[l][m], __ldg(g + kzf * gz));
             }
+        }
     }
 
-    line_fft<R, N, E, true, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
+    line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
-    if (c.valid) {
+    if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int j = t + T * m;
-            w[base + (long long)j * plane] = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + j));
-        }
+        for (int m = 0; m < E; ++m) col[(long long)(id.t + T * m) * plane] = v[0][m];
     }
 }
 
 // pass 3: inverse FFT along y + crop.  W2 -> W1.
-template <class Cfg, int SLOTS>
-__global__ void __launch_bounds__(SLOTS * Cfg::T)
+template <class Cfg, int SLOTS, int LPT>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>())
 k_y_inv(PassParams<typename Cfg::R> p) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
-    const int slot = threadIdx.x % SLOTS, t = threadIdx.x / SLOTS;
-    const int ny = p.ny, nz = p.nz;
-    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, nz, slot);
+    const ColIds<Cfg, SLOTS, LPT> id;
+    const int ny = p.ny;
+    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, p.nz, id.slot);
     const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
     cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
     const long long sx = p.sx;
 
-    cpx<R> v[2][E];
-    const long long ibase = (long long)c.other * 2 * ny * sx + c.kx;
+    cpx<R> v[LPT][E];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int l = 0; l < LPT; ++l) {
+        const cpx<R>* src = in + (long long)c.other * 2 * ny * sx + c.kx +
+                            (long long)(id.half(l) * ny + id.t) * sx;
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-            v[q][m] = c.valid ? in[ibase + (long long)(q * ny + t + T * m) * sx] : cpx<R>{0, 0};
+        for (int m = 0; m < E; ++m) v[l][m] = c.valid ? src[(long long)(T * m) * sx] : cpx<R>{0, 0};
+    }
+    LineSmem<R> ls[LPT];
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + id.half(l) * N * SLOTS + id.slot, SLOTS, 30, 0};
+    line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
-    const LineSmem<R> ls[2] = {{sm + slot, SLOTS, 30, 0}, {sm + N * SLOTS + slot, SLOTS, 30, 0}};
-    line_fft<R, N, E, true, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
-
-    if (c.valid) {
-        const long long obase = (long long)c.other * ny * sx + c.kx;
+    if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
+        cpx<R>* dst = out + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int j = t + T * m;
-            out[obase + (long long)j * sx] = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + j));
-        }
+        for (int m = 0; m < E; ++m) dst[(long long)(T * m) * sx] = v[0][m];
     }
 }
 
@@ -232,81 +290,117 @@ k_y_inv(PassParams<typename Cfg::R> p) {
 // Row passes (x axis; lines are contiguous rows, two real rows per line)
 // ==========================================================================
 //
-// Thread layout: t = tid % T (fastest), pair = tid / T.  A tile holds PAIRS
-// row pairs, i.e. 2*PAIRS consecutive rows, which are contiguous in rho/phi.
+// Thread = (t, pair[, q]): t fastest, then the row pair within the tile,
+// then (LPT = 1) the half q.  A tile holds PAIRS row pairs (2*PAIRS
+// consecutive rows, which are contiguous in rho and phi).
 
 template <class R> struct RowPad { static constexpr int SHIFT = sizeof(R) == 4 ? 4 : 3; };
 
 template <class Cfg> constexpr int row_line_stride() {
     return Cfg::N + (Cfg::N >> RowPad<typename Cfg::R>::SHIFT);
 }
+// real staging row stride: skews consecutive pairs' rows across banks
+template <class Cfg> constexpr int row_stage_stride() {
+    return Cfg::N + (Cfg::T >= 8 ? Cfg::T / 2 : 4);
+}
+template <class Cfg, int PAIRS, int LPT> constexpr int row_threads() {
+    return (LPT == 1 ? 2 : 1) * PAIRS * Cfg::T;
+}
+
+template <class Cfg, int PAIRS, int LPT> struct RowIds {
+    int t, pr, q;
+    __device__ __forceinline__ RowIds() {
+        t = threadIdx.x % Cfg::T;
+        pr = (threadIdx.x / Cfg::T) % PAIRS;
+        q = LPT == 1 ? threadIdx.x / (Cfg::T * PAIRS) : 0;
+    }
+    __device__ __forceinline__ int half(int l) const { return LPT == 2 ? l : q; }
+};
 
 // pass 0: pad + R2C along x.  rho (real rows of nx) -> W1 (nx+1 bins).
-template <class Cfg, int PAIRS>
-__global__ void __launch_bounds__(PAIRS * Cfg::T)
+template <class Cfg, int PAIRS, int LPT>
+__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>())
 k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     constexpr int LS = row_line_stride<Cfg>();
+    constexpr int RS = row_stage_stride<Cfg>();
     constexpr int SH = RowPad<R>::SHIFT;
-    constexpr int NT = PAIRS * T;
+    constexpr int NT = row_threads<Cfg, PAIRS, LPT>();
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(R);
+    constexpr int VPR = N / VW;  // vectors per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* stage = reinterpret_cast<R*>(smem_raw);
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
-    const int t = threadIdx.x % T, pr = threadIdx.x / T;
+    const RowIds<Cfg, PAIRS, LPT> id;
+    const int t = id.t, pr = id.pr;
     const int r0 = blockIdx.x * 2 * PAIRS;
     const int nrows = min(2 * PAIRS, rows - r0);
-    const R* __restrict__ in = static_cast<const R*>(p.in) + (long long)r0 * N;
-    cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
 
-    // stage the tile's rows (contiguous in rho) with 16-byte loads
+    // stage the tile's rows with 16-byte loads, all issued before any store
     {
-        using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-        constexpr int VW = 16 / sizeof(R);
-        const int nvec = nrows * N / VW;
-        const V* __restrict__ src = reinterpret_cast<const V*>(in);
-        V* dst = reinterpret_cast<V*>(stage);
-        for (int i = threadIdx.x; i < nvec; i += NT) dst[i] = __ldg(src + i);
+        const V* __restrict__ src = reinterpret_cast<const V*>(static_cast<const R*>(p.in) + (long long)r0 * N);
+        constexpr int PER = (2 * PAIRS * VPR + NT - 1) / NT;
+        V buf[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = threadIdx.x + u * NT;
+            if (i < nrows * VPR) buf[u] = __ldg(src + i);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = threadIdx.x + u * NT;
+            if (i < nrows * VPR) {
+                const int s = i / VPR, c = i - s * VPR;
+                *reinterpret_cast<V*>(stage + s * RS + c * VW) = buf[u];
+            }
+        }
     }
     __syncthreads();
-    cpx<R> v[2][E];
+    cpx<R> v[LPT][E];
     const bool has_a = 2 * pr < nrows, has_b = 2 * pr + 1 < nrows;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int j = t + T * m;
-        const R a = has_a ? stage[(2 * pr) * N + j] : (R)0;
-        const R b = has_b ? stage[(2 * pr + 1) * N + j] : (R)0;
+        const R a = has_a ? stage[(2 * pr) * RS + j] : (R)0;
+        const R b = has_b ? stage[(2 * pr + 1) * RS + j] : (R)0;
         v[0][m] = {a, b};
     }
     __syncthreads();  // the staging area becomes the line buffers
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[1][m] = cmul(v[0][m], ldg_c(p.tw + t + T * m));
-
-    const LineSmem<R> ls[2] = {{sm + (0 * PAIRS + pr) * LS, 1, SH, 1},
-                               {sm + (1 * PAIRS + pr) * LS, 1, SH, 1}};
-    line_fft<R, N, E, false, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
+    for (int l = 0; l < LPT; ++l) {
+        if (id.half(l)) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+            for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + t + T * m));
+        }
+    }
+    LineSmem<R> ls[LPT];
 #pragma unroll
-        for (int m = 0; m < E; ++m) ls[q][t + T * m] = v[q][m];
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + (id.half(l) * PAIRS + pr) * LS, 1, SH, 1};
+    line_fft<R, N, E, false, LPT>(v, t, ls, p.tw, typename Cfg::Rads{});
+#pragma unroll
+    for (int l = 0; l < LPT; ++l)
+#pragma unroll
+        for (int m = 0; m < E; ++m) ls[l][t + T * m] = v[l][m];
     __syncthreads();
 
     // separate the two rows' spectra: A[k] = (Z[k] + conj Z[2N-k]) / 2,
     // B[k] = -i (Z[k] - conj Z[2N-k]) / 2, k = 0..N; Z[2k'] = E[k'],
     // Z[2k'+1] = O[k'].
+    cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
     const long long sx = p.sx;
     const int nout = nrows * (N + 1);
     for (int i = threadIdx.x; i < nout; i += NT) {
         const int s = i / (N + 1), k = i - s * (N + 1);
         const int pp = s >> 1;
+        const int kh = k >> 1;
         cpx<R> P, Q;
         if ((k & 1) == 0) {
-            const int kh = k >> 1;
             const LineSmem<R> e = {sm + pp * LS, 1, SH, 1};
             P = e[kh];
             Q = e[kh == 0 ? 0 : N - kh];
         } else {
-            const int kh = k >> 1;
             const LineSmem<R> o = {sm + (PAIRS + pp) * LS, 1, SH, 1};
             P = o[kh];
             Q = o[N - 1 - kh];
@@ -320,143 +414,209 @@ k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
 }
 
 // pass 4: C2R along x + crop.  W1 (nx+1 bins) -> phi (real rows of nx).
-template <class Cfg, int PAIRS>
-__global__ void __launch_bounds__(PAIRS * Cfg::T)
+template <class Cfg, int PAIRS, int LPT>
+__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>())
 k_x_inv(PassParams<typename Cfg::R> p, int rows) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     constexpr int LS = row_line_stride<Cfg>();
+    constexpr int RS = row_stage_stride<Cfg>();
     constexpr int SH = RowPad<R>::SHIFT;
-    constexpr int NT = PAIRS * T;
+    constexpr int NT = row_threads<Cfg, PAIRS, LPT>();
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(R);
+    constexpr int VPR = N / VW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     R* stage = reinterpret_cast<R*>(smem_raw);
-    const int t = threadIdx.x % T, pr = threadIdx.x / T;
+    const RowIds<Cfg, PAIRS, LPT> id;
+    const int t = id.t, pr = id.pr;
     const int r0 = blockIdx.x * 2 * PAIRS;
     const int nrows = min(2 * PAIRS, rows - r0);
-    const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
     const long long sx = p.sx;
 
-    // stage the spectra rows: row s occupies [s*(N+1), (s+1)*(N+1))
-    const int nin = nrows * (N + 1);
-    for (int i = threadIdx.x; i < nin; i += NT) {
-        const int s = i / (N + 1), k = i - s * (N + 1);
-        sm[i] = in[(long long)(r0 + s) * sx + k];
+    // stage the spectra rows (row s at [s*(N+1), (s+1)*(N+1))), loads first
+    {
+        const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
+        constexpr int PER = (2 * PAIRS * (N + 1) + NT - 1) / NT;
+        cpx<R> buf[PER];
+        const int nin = nrows * (N + 1);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = threadIdx.x + u * NT;
+            if (i < nin) {
+                const int s = i / (N + 1), k = i - s * (N + 1);
+                buf[u] = in[(long long)(r0 + s) * sx + k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = threadIdx.x + u * NT;
+            if (i < nin) sm[i] = buf[u];
+        }
     }
     __syncthreads();
-    // Z[k] = A[k] + i B[k] with A[2N-k] = conj A[k] (same for B)
-    cpx<R> v[2][E];
+    // Z[k] = A[k] + i B[k] with A[2N-k] = conj A[k] (same for B); register
+    // line l holds Z[2k' + half(l)], k' = t + T m.
+    cpx<R> v[LPT][E];
     const bool has_a = 2 * pr < nrows, has_b = 2 * pr + 1 < nrows;
     const cpx<R>* ra = sm + (2 * pr) * (N + 1);
     const cpx<R>* rb = sm + (2 * pr + 1) * (N + 1);
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int l = 0; l < LPT; ++l)
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            const int k = 2 * (t + T * m) + q;
+            const int k = 2 * (t + T * m) + id.half(l);
             const bool lo = k <= N;
             const int kk = lo ? k : 2 * N - k;
             const cpx<R> a = has_a ? ra[kk] : cpx<R>{0, 0};
             const cpx<R> b = has_b ? rb[kk] : cpx<R>{0, 0};
-            v[q][m] = lo ? cpx<R>{a.x - b.y, a.y + b.x} : cpx<R>{a.x + b.y, b.x - a.y};
+            v[l][m] = lo ? cpx<R>{a.x - b.y, a.y + b.x} : cpx<R>{a.x + b.y, b.x - a.y};
         }
     __syncthreads();  // the staging area becomes the line buffers
 
-    const LineSmem<R> ls[2] = {{sm + (0 * PAIRS + pr) * LS, 1, SH, 1},
-                               {sm + (1 * PAIRS + pr) * LS, 1, SH, 1}};
-    line_fft<R, N, E, true, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
-    __syncthreads();  // line buffers become the output staging area
-
-    // z[j] = a[j] + W_2N^-j b[j]; real part -> row 2 pr, imaginary -> 2 pr + 1
+    LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int j = t + T * m;
-        const cpx<R> z = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + j));
-        stage[(2 * pr) * N + j] = z.x;
-        stage[(2 * pr + 1) * N + j] = z.y;
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + (id.half(l) * PAIRS + pr) * LS, 1, SH, 1};
+    line_fft<R, N, E, true, LPT>(v, t, ls, p.tw, typename Cfg::Rads{});
+
+    // z[j] = a[j] + W_2N^-j b[j]
+    bool holder = true;
+    if constexpr (LPT == 2) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + t + T * m));
+    } else {
+        const LineSmem<R> lodd = {sm + (PAIRS + pr) * LS, 1, SH, 1};
+        if (id.q) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int j = t + T * m;
+                lodd[j] = cmulc(v[0][m], ldg_c(p.tw + j));
+            }
+        }
+        __syncthreads();
+        if (!id.q) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + lodd[t + T * m];
+        }
+        holder = id.q == 0;
+    }
+    __syncthreads();  // line buffers become the output staging area
+    if (holder) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int j = t + T * m;
+            stage[(2 * pr) * RS + j] = v[0][m].x;
+            stage[(2 * pr + 1) * RS + j] = v[0][m].y;
+        }
     }
     __syncthreads();
     {
-        using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-        constexpr int VW = 16 / sizeof(R);
-        const int nvec = nrows * N / VW;
         V* dst = reinterpret_cast<V*>(static_cast<R*>(p.out) + (long long)r0 * N);
-        const V* src = reinterpret_cast<const V*>(stage);
-        for (int i = threadIdx.x; i < nvec; i += NT) dst[i] = src[i];
+        constexpr int PER = (2 * PAIRS * VPR + NT - 1) / NT;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = threadIdx.x + u * NT;
+            if (i < nrows * VPR) {
+                const int s = i / VPR, c = i - s * VPR;
+                dst[i] = *reinterpret_cast<const V*>(stage + s * RS + c * VW);
+            }
+        }
     }
 }
 
 // ==========================================================================
-// launch helpers
+// launch helpers and variants
 // ==========================================================================
-template <class Cfg> constexpr int col_slots() {
-    constexpr int XW = Seg<typename Cfg::R>::XW;
-    constexpr int s = 256 / Cfg::T;
-    return s < XW ? XW : s;
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per
+// kernel and device (Tag makes one flag set per kernel instantiation).
+template <class Tag, class K> inline cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static unsigned long long done = 0;  // bit d: attribute set on device d
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done |= bit;
+    return e;
 }
-template <class Cfg> constexpr int row_pairs() {
-    constexpr int s = 256 / Cfg::T;
+template <int PASS, class Cfg, int A, int B> struct SmemTag {};
+
+// A variant fixes lines per thread and the CTA's target thread count; the
+// tile width (column passes: SLOTS lines, row passes: PAIRS row pairs)
+// follows from the line's thread count T.
+template <int LPT_, int THREADS_> struct Var {
+    static constexpr int LPT = LPT_;
+    static constexpr int THREADS = THREADS_;
+};
+
+template <class Cfg, class V> constexpr int var_slots() {
+    constexpr int XW = Seg<typename Cfg::R>::XW;
+    constexpr int lo = XW / 2 < 8 ? 8 : XW / 2;           // >= 64-byte row segments
+    constexpr int s = V::THREADS / ((V::LPT == 1 ? 2 : 1) * Cfg::T);
+    return s < lo ? lo : s;
+}
+template <class Cfg, class V> constexpr int var_pairs() {
+    constexpr int s = V::THREADS / ((V::LPT == 1 ? 2 : 1) * Cfg::T);
     return s < 1 ? 1 : s;
 }
-template <class Cfg> constexpr size_t col_smem() {
-    return 2ull * Cfg::N * col_slots<Cfg>() * sizeof(cpx<typename Cfg::R>);
+template <class Cfg, int SLOTS> constexpr size_t col_smem() {
+    return 2ull * Cfg::N * SLOTS * sizeof(cpx<typename Cfg::R>);
 }
-template <class Cfg> constexpr size_t row_smem() {
+template <class Cfg, int PAIRS> constexpr size_t row_smem() {
     using R = typename Cfg::R;
-    constexpr int P = row_pairs<Cfg>();
-    constexpr size_t lines = 2ull * P * row_line_stride<Cfg>() * sizeof(cpx<R>);
-    constexpr size_t stage_c = 2ull * P * (Cfg::N + 1) * sizeof(cpx<R>);
-    constexpr size_t stage_r = 2ull * P * Cfg::N * sizeof(R);
+    constexpr size_t lines = 2ull * PAIRS * row_line_stride<Cfg>() * sizeof(cpx<R>);
+    constexpr size_t stage_c = 2ull * PAIRS * (Cfg::N + 1) * sizeof(cpx<R>);
+    constexpr size_t stage_r = 2ull * PAIRS * row_stage_stride<Cfg>() * sizeof(R);
     constexpr size_t m1 = lines > stage_c ? lines : stage_c;
     return m1 > stage_r ? m1 : stage_r;
 }
 
-template <class K> inline cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 // pass ids: 0 x_fwd, 1 y_fwd, 2 z_conv, 3 y_inv, 4 x_inv
-template <class Cfg>
+template <class Cfg, class V>
 cudaError_t launch_row(int pass, const PassParams<typename Cfg::R>& p, int rows, cudaStream_t st) {
-    constexpr int P = row_pairs<Cfg>();
-    constexpr size_t sm = row_smem<Cfg>();
+    constexpr int P = var_pairs<Cfg, V>();
+    constexpr int L = V::LPT;
+    constexpr size_t sm = row_smem<Cfg, P>();
+    constexpr int NT = row_threads<Cfg, P, L>();
+    static_assert(NT <= 1024, "row CTA too large");
     const int grid = (rows + 2 * P - 1) / (2 * P);
     if (grid == 0) return cudaSuccess;
     cudaError_t e;
     if (pass == 0) {
-        e = set_smem(k_x_fwd<Cfg, P>, sm);
-        if (e != cudaSuccess) return e;
-        k_x_fwd<Cfg, P><<<grid, P * Cfg::T, sm, st>>>(p, rows);
+        if ((e = set_smem<SmemTag<0, Cfg, P, L>>(k_x_fwd<Cfg, P, L>, sm)) != cudaSuccess) return e;
+        k_x_fwd<Cfg, P, L><<<grid, NT, sm, st>>>(p, rows);
     } else {
-        e = set_smem(k_x_inv<Cfg, P>, sm);
-        if (e != cudaSuccess) return e;
-        k_x_inv<Cfg, P><<<grid, P * Cfg::T, sm, st>>>(p, rows);
+        if ((e = set_smem<SmemTag<4, Cfg, P, L>>(k_x_inv<Cfg, P, L>, sm)) != cudaSuccess) return e;
+        k_x_inv<Cfg, P, L><<<grid, NT, sm, st>>>(p, rows);
     }
     return cudaGetLastError();
 }
 
-template <class Cfg>
+template <class Cfg, class V>
 cudaError_t launch_col(int pass, const PassParams<typename Cfg::R>& p, cudaStream_t st) {
     using R = typename Cfg::R;
-    constexpr int S = col_slots<Cfg>();
-    constexpr size_t sm = col_smem<Cfg>();
-    const int L = pass == 2 ? 2 * p.ny : p.nz;
-    const int grid = col_grid<R, S>(p.nx + 1, L);
+    constexpr int S = var_slots<Cfg, V>();
+    constexpr int L = V::LPT;
+    constexpr size_t sm = col_smem<Cfg, S>();
+    constexpr int NT = col_threads<Cfg, S, L>();
+    static_assert(NT <= 1024, "column CTA too large");
+    const int lines = pass == 2 ? 2 * p.ny : p.nz;
+    const int grid = col_grid<R, S>(p.nx + 1, lines);
     if (grid == 0) return cudaSuccess;
     cudaError_t e;
     if (pass == 1) {
-        e = set_smem(k_y_fwd<Cfg, S>, sm);
-        if (e != cudaSuccess) return e;
-        k_y_fwd<Cfg, S><<<grid, S * Cfg::T, sm, st>>>(p);
+        if ((e = set_smem<SmemTag<1, Cfg, S, L>>(k_y_fwd<Cfg, S, L>, sm)) != cudaSuccess) return e;
+        k_y_fwd<Cfg, S, L><<<grid, NT, sm, st>>>(p);
     } else if (pass == 3) {
-        e = set_smem(k_y_inv<Cfg, S>, sm);
-        if (e != cudaSuccess) return e;
-        k_y_inv<Cfg, S><<<grid, S * Cfg::T, sm, st>>>(p);
+        if ((e = set_smem<SmemTag<3, Cfg, S, L>>(k_y_inv<Cfg, S, L>, sm)) != cudaSuccess) return e;
+        k_y_inv<Cfg, S, L><<<grid, NT, sm, st>>>(p);
     } else {
-        e = set_smem(k_z_conv<Cfg, S>, sm);
-        if (e != cudaSuccess) return e;
-        k_z_conv<Cfg, S><<<grid, S * Cfg::T, sm, st>>>(p);
+        if ((e = set_smem<SmemTag<2, Cfg, S, L>>(k_z_conv<Cfg, S, L>, sm)) != cudaSuccess) return e;
+        k_z_conv<Cfg, S, L><<<grid, NT, sm, st>>>(p);
     }
     return cudaGetLastError();
 }

@@ -283,3 +283,41 @@ def test_bad_arguments_on_device(pg):
         rc = pg.lib().poisson_solve(plan.handle, ctypes.c_void_p(flat.data_ptr() + 4),
                                     ctypes.c_void_p(x.data_ptr()), None)
         assert rc == 1
+
+
+# ---------------------------------------------------------------------------
+# kernel variants and the autotuner
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (48, 32, 96), (64, 128, 192), (16, 256, 48),
+                                   (32, 16, 384), (512, 16, 32), (16, 512, 16)])
+def test_every_kernel_variant_matches_oracle(pg, oracle_mod, shape):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(sum(shape) + 1)
+    rho = rng.standard_normal(shape).astype(np.float32)
+    h = (1.0, 0.75, 1.25)
+    ref = oracle_mod.solve_fft(rho.astype(np.float64), h=h)
+    x = torch.from_numpy(rho).cuda()
+    with pg.Plan(nx, ny, nz, h=h) as plan:
+        counts = plan.info()["variant_count"]
+        for v in range(max(counts)):
+            for pss in range(5):
+                plan.set_variant(pss, min(v, counts[pss] - 1))
+            out = plan.solve(x).double().cpu().numpy()
+            l2, mx = rel_errors(out, ref)
+            assert l2 <= TOL32[0] and mx <= TOL32[1], (v, l2, mx)
+
+
+def test_autotuned_plan_matches_oracle(pg, oracle_mod):
+    shape = (64, 96, 128)
+    rho = np.random.default_rng(9).standard_normal(shape).astype(np.float32)
+    ref = oracle_mod.solve_fft(rho.astype(np.float64))
+    with pg.Plan(128, 96, 64, flags=pg.abi.FLAG_AUTOTUNE) as plan:
+        info = plan.info()
+        assert all(0 <= v < c for v, c in zip(info["variant"], info["variant_count"]))
+        out = plan.solve(torch.from_numpy(rho).cuda()).double().cpu().numpy()
+        plan.autotune()
+        out2 = plan.solve(torch.from_numpy(rho).cuda()).double().cpu().numpy()
+    for o in (out, out2):
+        l2, mx = rel_errors(o, ref)
+        assert l2 <= TOL32[0] and mx <= TOL32[1]
