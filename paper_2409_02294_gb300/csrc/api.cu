@@ -8,29 +8,11 @@
 
 #include "configs.cuh"
 #include "internal.h"
+#include "plan.h"
 #include "poisson.h"
 
 using namespace pgb;
 
-struct poisson_plan_s {
-    int nx, ny, nz;
-    double hx, hy, hz, G;
-    poisson_precision prec;
-    unsigned flags;
-    int r_near;
-    int device;
-    long long sx;         // complex row stride of W1/W2
-    size_t csize;         // bytes per complex element
-    size_t rsize;         // bytes per real element
-    void* w1;             // nz * ny * sx complex
-    void* w2;             // nz * 2ny * sx complex
-    void* greens;         // (nx+1)(ny+1)(nz+1) real
-    void* tw[3];          // W_{2n}^j tables for x, y, z
-    unsigned* status;     // device status word
-    void* stage_in;       // device staging for poisson_solve_host
-    void* stage_out;
-    int var[5];           // kernel variant per pass (autotuned or default)
-};
 
 namespace {
 
@@ -294,6 +276,7 @@ poisson_status poisson_plan_create(poisson_plan_t* out, int nx, int ny, int nz, 
 poisson_status poisson_plan_destroy(poisson_plan_t plan) {
     if (!plan) return POISSON_ERR_ARG;
     cudaDeviceSynchronize();
+    pgb::batch_forget_plan(plan);
     free_plan(plan);
     return POISSON_OK;
 }
@@ -399,16 +382,11 @@ poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream) 
 poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count, const void* const* rho_dev,
                                      void* const* phi_dev, void* cuda_stream) {
     if (count < 0 || (count > 0 && (!plans || !rho_dev || !phi_dev))) return POISSON_ERR_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     for (int i = 0; i < count; ++i) {
         poisson_status s = check_io(plans[i], rho_dev[i], phi_dev[i]);
         if (s != POISSON_OK) return s;
     }
-    for (int i = 0; i < count; ++i) {
-        poisson_status s = solve_all(plans[i], rho_dev[i], phi_dev[i], st);
-        if (s != POISSON_OK) return s;
-    }
-    return POISSON_OK;
+    return pgb::batched_solve(plans, count, rho_dev, phi_dev, static_cast<cudaStream_t>(cuda_stream));
 }
 
 }  // extern "C"

@@ -60,6 +60,23 @@ template <class R> __device__ __forceinline__ cpx<R> ldg_c(const cpx<R>* p) {
     }
 }
 
+// Load of data that this kernel launch may also have written elsewhere on
+// the GPU: CG = true bypasses L1 (ld.global.cg), which is required when a
+// persistent kernel reads data produced by other SMs in the same launch.
+template <bool CG, class R> __device__ __forceinline__ cpx<R> ld_c(const cpx<R>* p) {
+    if constexpr (CG) {
+        if constexpr (std::is_same<R, float>::value) {
+            float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+            return {v.x, v.y};
+        } else {
+            double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+            return {v.x, v.y};
+        }
+    } else {
+        return *p;
+    }
+}
+
 // --------------------------------------------------------------------------
 // compile-time twiddles: W_n^e = exp(-2 pi i e / n) for n dividing 96
 // --------------------------------------------------------------------------

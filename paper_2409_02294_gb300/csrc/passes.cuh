@@ -62,14 +62,14 @@ template <class R, int SLOTS> struct ColTile {
 };
 
 template <class R, int SLOTS>
-__device__ __forceinline__ ColTile<R, SLOTS> col_tile(int ncols, int L, int slot) {
+__device__ __forceinline__ ColTile<R, SLOTS> col_tile(int ncols, int L, int slot, int tile) {
     constexpr int XW = SLOTS < Seg<R>::XW ? SLOTS : Seg<R>::XW;
     constexpr int NLW = SLOTS / XW;
     const int nxw = ncols / XW;
     const int wide_l = (L + NLW - 1) / NLW;
     const int n_wide = nxw * wide_l;
     ColTile<R, SLOTS> c;
-    int b = blockIdx.x;
+    int b = tile;
     if (b < n_wide) {
         const int xt = b % nxw, lt = b / nxw;
         c.kx = xt * XW + slot % XW;
@@ -117,16 +117,15 @@ template <class Cfg, int SLOTS, int LPT> constexpr int col_threads() {
 }
 
 // pass 1: pad + forward FFT along y.  W1 -> W2.
-template <class Cfg, int SLOTS, int LPT>
-__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>())
-k_y_fwd(PassParams<typename Cfg::R> p) {
+template <class Cfg, int SLOTS, int LPT, bool CG>
+__device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p, int tile,
+                                            unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     const ColIds<Cfg, SLOTS, LPT> id;
     const int ny = p.ny;
-    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, p.nz, id.slot);
+    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, p.nz, id.slot, tile);
     const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
     cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
     const long long sx = p.sx;
@@ -134,7 +133,7 @@ k_y_fwd(PassParams<typename Cfg::R> p) {
     cpx<R> v[LPT][E];
     const cpx<R>* src = in + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[0][m] = c.valid ? src[(long long)(T * m) * sx] : cpx<R>{0, 0};
+    for (int m = 0; m < E; ++m) v[0][m] = c.valid ? ld_c<CG>(src + (long long)(T * m) * sx) : cpx<R>{0, 0};
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
@@ -193,16 +192,15 @@ __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cf
 // pass 2: pad + FFT along z, multiply by Ghat, inverse FFT along z, crop.
 // In place on W2.  Ghat is real (the kernel is real and even), so the
 // adjoint's conj(Ghat) is the same multiply.
-template <class Cfg, int SLOTS, int LPT>
-__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>())
-k_z_conv(PassParams<typename Cfg::R> p) {
+template <class Cfg, int SLOTS, int LPT, bool CG>
+__device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p, int tile,
+                                            unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     const ColIds<Cfg, SLOTS, LPT> id;
     const int nx = p.nx, ny = p.ny;
-    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(nx + 1, 2 * ny, id.slot);
+    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(nx + 1, 2 * ny, id.slot, tile);
     cpx<R>* __restrict__ w = static_cast<cpx<R>*>(p.out);
     const long long plane = 2LL * ny * p.sx;
 
@@ -210,7 +208,7 @@ k_z_conv(PassParams<typename Cfg::R> p) {
     cpx<R>* col = w + (long long)c.other * p.sx + c.kx;
 #pragma unroll
     for (int m = 0; m < E; ++m)
-        v[0][m] = c.valid ? col[(long long)(id.t + T * m) * plane] : cpx<R>{0, 0};
+        v[0][m] = c.valid ? ld_c<CG>(col + (long long)(id.t + T * m) * plane) : cpx<R>{0, 0};
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
@@ -252,16 +250,15 @@ k_z_conv(PassParams<typename Cfg::R> p) {
 }
 
 // pass 3: inverse FFT along y + crop.  W2 -> W1.
-template <class Cfg, int SLOTS, int LPT>
-__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>())
-k_y_inv(PassParams<typename Cfg::R> p) {
+template <class Cfg, int SLOTS, int LPT, bool CG>
+__device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p, int tile,
+                                            unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     const ColIds<Cfg, SLOTS, LPT> id;
     const int ny = p.ny;
-    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, p.nz, id.slot);
+    const ColTile<R, SLOTS> c = col_tile<R, SLOTS>(p.nx + 1, p.nz, id.slot, tile);
     const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
     cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
     const long long sx = p.sx;
@@ -272,7 +269,7 @@ k_y_inv(PassParams<typename Cfg::R> p) {
         const cpx<R>* src = in + (long long)c.other * 2 * ny * sx + c.kx +
                             (long long)(id.half(l) * ny + id.t) * sx;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[l][m] = c.valid ? src[(long long)(T * m) * sx] : cpx<R>{0, 0};
+        for (int m = 0; m < E; ++m) v[l][m] = c.valid ? ld_c<CG>(src + (long long)(T * m) * sx) : cpx<R>{0, 0};
     }
     LineSmem<R> ls[LPT];
 #pragma unroll
@@ -318,9 +315,9 @@ template <class Cfg, int PAIRS, int LPT> struct RowIds {
 };
 
 // pass 0: pad + R2C along x.  rho (real rows of nx) -> W1 (nx+1 bins).
-template <class Cfg, int PAIRS, int LPT>
-__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>())
-k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
+template <class Cfg, int PAIRS, int LPT, bool CG>
+__device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p, int rows, int tile,
+                                            unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     constexpr int LS = row_line_stride<Cfg>();
@@ -330,12 +327,11 @@ k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
     using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
     constexpr int VW = 16 / sizeof(R);
     constexpr int VPR = N / VW;  // vectors per row
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R* stage = reinterpret_cast<R*>(smem_raw);
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     const RowIds<Cfg, PAIRS, LPT> id;
     const int t = id.t, pr = id.pr;
-    const int r0 = blockIdx.x * 2 * PAIRS;
+    const int r0 = tile * 2 * PAIRS;
     const int nrows = min(2 * PAIRS, rows - r0);
 
     // stage the tile's rows with 16-byte loads, all issued before any store
@@ -414,9 +410,9 @@ k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
 }
 
 // pass 4: C2R along x + crop.  W1 (nx+1 bins) -> phi (real rows of nx).
-template <class Cfg, int PAIRS, int LPT>
-__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>())
-k_x_inv(PassParams<typename Cfg::R> p, int rows) {
+template <class Cfg, int PAIRS, int LPT, bool CG>
+__device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p, int rows, int tile,
+                                            unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     constexpr int LS = row_line_stride<Cfg>();
@@ -426,12 +422,11 @@ k_x_inv(PassParams<typename Cfg::R> p, int rows) {
     using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
     constexpr int VW = 16 / sizeof(R);
     constexpr int VPR = N / VW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     R* stage = reinterpret_cast<R*>(smem_raw);
     const RowIds<Cfg, PAIRS, LPT> id;
     const int t = id.t, pr = id.pr;
-    const int r0 = blockIdx.x * 2 * PAIRS;
+    const int r0 = tile * 2 * PAIRS;
     const int nrows = min(2 * PAIRS, rows - r0);
     const long long sx = p.sx;
 
@@ -446,7 +441,7 @@ k_x_inv(PassParams<typename Cfg::R> p, int rows) {
             const int i = threadIdx.x + u * NT;
             if (i < nin) {
                 const int s = i / (N + 1), k = i - s * (N + 1);
-                buf[u] = in[(long long)(r0 + s) * sx + k];
+                buf[u] = ld_c<CG>(in + (long long)(r0 + s) * sx + k);
             }
         }
 #pragma unroll
@@ -523,6 +518,35 @@ k_x_inv(PassParams<typename Cfg::R> p, int rows) {
             }
         }
     }
+}
+
+// ==========================================================================
+// kernels: one tile per CTA
+// ==========================================================================
+template <class Cfg, int SLOTS, int LPT>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>()) k_y_fwd(PassParams<typename Cfg::R> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_y_fwd<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
+}
+template <class Cfg, int SLOTS, int LPT>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>()) k_z_conv(PassParams<typename Cfg::R> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_z_conv<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
+}
+template <class Cfg, int SLOTS, int LPT>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>()) k_y_inv(PassParams<typename Cfg::R> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_y_inv<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
+}
+template <class Cfg, int PAIRS, int LPT>
+__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>()) k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_x_fwd<Cfg, PAIRS, LPT, false>(p, rows, blockIdx.x, smem_raw);
+}
+template <class Cfg, int PAIRS, int LPT>
+__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>()) k_x_inv(PassParams<typename Cfg::R> p, int rows) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_x_inv<Cfg, PAIRS, LPT, false>(p, rows, blockIdx.x, smem_raw);
 }
 
 // ==========================================================================

@@ -1,0 +1,36 @@
+// The plan object behind poisson_plan_t (shared by the library's units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "poisson.h"
+
+struct poisson_plan_s {
+    int nx, ny, nz;
+    double hx, hy, hz, G;
+    poisson_precision prec;
+    unsigned flags;
+    int r_near;
+    int device;
+    long long sx;         // complex row stride of W1/W2
+    size_t csize;         // bytes per complex element
+    size_t rsize;         // bytes per real element
+    void* w1;             // nz * ny * sx complex
+    void* w2;             // nz * 2ny * sx complex
+    void* greens;         // (nx+1)(ny+1)(nz+1) real
+    void* tw[3];          // W_{2n}^j tables for x, y, z
+    unsigned* status;     // device status word
+    void* stage_in;       // device staging for poisson_solve_host
+    void* stage_out;
+    int var[5];           // kernel variant per pass (autotuned or default)
+};
+
+namespace pgb {
+// Drop every cached batched-solve graph that refers to `plan` (called when
+// the plan is destroyed).
+void batch_forget_plan(poisson_plan_t plan);
+// The batched solve (poisson_solve_batched after argument checks).
+poisson_status batched_solve(poisson_plan_t const* plans, int count, const void* const* rho,
+                             void* const* phi, cudaStream_t st);
+}  // namespace pgb
