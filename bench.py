@@ -38,6 +38,9 @@ WORKLOADS = {
                        "background, unit spacing, G=1, zero-padded to 512^3"),
     "lognormal512": dict(n=512, desc="512^3 cells FP32, seeded lognormal field (sigma 1.5, "
                          "k^-3 spectrum) + uniform ball r=40, zero-padded to 1024^3"),
+    "plummer384x8": dict(n=384, fields=8, desc="8 fields of 384^3 cells, 16 seeded Plummer "
+                         "spheres each + 1% uniform background, zero-padded to 768^3 "
+                         "(radix-3 sizes), solved one after another with one plan"),
     "batch96": dict(n=None, desc="96 FP32 fields, edges from {64,96,128,192,256,384}, half "
                     "cubic / half 2:1, 4-16 seeded Gaussian blobs each, one persistent "
                     "graph-replayed launch per batch"),
@@ -49,6 +52,8 @@ def make_density(name, seed):
     n = WORKLOADS[name]["n"]
     if name == "plummer256":
         rho, _ = workloads.plummer_spheres(n, count=64, seed=seed)
+    elif name == "plummer384x8":
+        rho, _ = workloads.plummer_spheres(n, count=16, seed=seed)
     else:
         rho, _ = workloads.lognormal_field(n, seed=seed)
     return rho.astype(np.float32)
@@ -296,29 +301,31 @@ def run_ours(args):
 
     wl = args.workload
     n = WORKLOADS[wl]["n"]
-    rho32 = make_density(wl, args.seed + rank)
-    rho = torch.from_numpy(rho32).to(dev)
-    phi = torch.empty_like(rho)
-    plan = pg.Plan(n, n, n, precision="fp32", flags=pg.abi.FLAG_AUTOTUNE)
+    nf = WORKLOADS[wl].get("fields", 1)
+    rhos32 = [make_density(wl, args.seed + rank * nf + i) for i in range(nf)]
+    rho32 = rhos32[0]
+    rhos = [torch.from_numpy(r).to(dev) for r in rhos32]
+    phis = [torch.empty_like(r) for r in rhos]
+    rho, phi = rhos[0], phis[0]
+    plan = pg.Plan(n, n, n, precision=args.precision, flags=pg.abi.FLAG_AUTOTUNE)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(evs=None):
-        if evs is None:
+        for f in range(nf):
+            if evs is not None and f == 0:
+                evs[0].record(stream)
             for i in range(5):
-                plan.solve_pass(i, rho, phi, stream)
-            return
-        evs[0].record(stream)
-        for i in range(5):
-            plan.solve_pass(i, rho, phi, stream)
-            evs[i + 1].record(stream)
+                plan.solve_pass(i, rhos[f], phis[f], stream)
+                if evs is not None:
+                    evs[f * 5 + i + 1].record(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
 
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5 * nf + 1)] for _ in range(args.steps)]
     props = torch.cuda.get_device_properties(dev)
     gpu_id = "GPU-" + str(props.uuid) if hasattr(props, "uuid") else str(dev.index)
     sampler = ClockSampler(gpu_id)
@@ -334,14 +341,15 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
 
-    step_ms = [ev[0].elapsed_time(ev[5]) for ev in events]
-    pass_ms = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in events) / args.steps for i in range(5)]
+    step_ms = [ev[0].elapsed_time(ev[5 * nf]) for ev in events]
+    pass_ms = [sum(ev[f * 5 + i].elapsed_time(ev[f * 5 + i + 1]) for ev in events for f in range(nf))
+               / (args.steps * nf) for i in range(5)]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    cells = n ** 3
+    cells = n ** 3 * nf
     value = world * cells * args.steps / (total_ms / 1e3)
 
     # accuracy of this run's output against the FP64 oracle, and the oracle
@@ -349,12 +357,13 @@ def run_ours(args):
     cpu = None
     acc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, ref = cpu_oracle_time(rho32, reps=2, min_seconds=8.0)
+        times, ref = cpu_oracle_time(rho32, reps=2, min_seconds=8.0 if nf == 1 else 0.0)
         out = phi.double().cpu().numpy()
         acc = {"rel_l2": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
                "max_rel": float(np.abs(out - ref).max() / np.abs(ref).max()),
-               "tolerance_rel_l2": TOL_REL_L2, "reference": "FP64 oracle, full field"}
-        cpu = {"value": cells / statistics.median(times), "unit": UNIT, "cores": os.cpu_count(),
+               "tolerance_rel_l2": TOL_REL_L2 if args.precision in ("fp32", "tc_fp16x2") else 5e-5,
+               "reference": "FP64 oracle, full field" + (" (field 0)" if nf > 1 else "")}
+        cpu = {"value": n ** 3 / statistics.median(times), "unit": UNIT, "cores": os.cpu_count(),
                "kind": "oracle",
                "sample": "full %d^3 field, oracle FFT-convolution route (scipy.fft FP64, all "
                          "host cores), %d solves, median" % (n, len(times))}
@@ -362,7 +371,7 @@ def run_ours(args):
     # end to end through the C-ABI host-buffer call: H2D + solve + D2H per step
     e2e = None
     if not args.no_e2e:
-        host_in = torch.from_numpy(rho32).pin_memory()
+        host_in = torch.from_numpy(rhos32[0]).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         for _ in range(3):
             plan.solve_host(host_in, host_out, stream)
@@ -376,11 +385,13 @@ def run_ours(args):
             t = torch.tensor([te], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
-        e2e = {"value": world * cells * ksteps / te, "unit": UNIT,
+        e2e = {"value": world * n ** 3 * ksteps / te, "unit": UNIT,
                "h2d_bytes_per_step": rho32.nbytes, "d2h_bytes_per_step": rho32.nbytes,
                "steps": ksteps}
 
     dom = int(np.argmax(pass_ms))
+    if args.precision != "fp32":
+        KERNEL_NAMES[2] = "k_z_conv_tc"
     pb = pass_bytes(n, n, n)
     peak, peak_kind = peaks()
     achieved = pb[dom] / (pass_ms[dom] / 1e3) / 1e9
@@ -390,9 +401,10 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f32+%s" % args.precision[3:],
             "data": "synthetic",
-            "config": {"workload": wl, "description": WORKLOADS[wl]["desc"],
+            "config": {"workload": wl, "description": WORKLOADS[wl]["desc"], "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": "independent field per GPU" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
@@ -407,7 +419,7 @@ def run_ours(args):
             "accuracy": acc,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 5 * nf * args.steps,
             "kernel_variants": plan.info()["variant"],
             "clocks": clocks,
             "wall_s_timed": t_wall,
@@ -427,6 +439,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plummer256")
     ap.add_argument("--seed", type=int, default=2409)
+    ap.add_argument("--precision", choices=["fp32", "tc_fp16x2", "tc_bf16x2"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -167,8 +167,8 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
 
 /*
  * Autotuner: for each of the five passes, time every compiled kernel variant
- * (lines per thread, CTA shape) on the plan's own buffers (one warm-up and
- * three timed launches each, CUDA events on cuda_stream) and keep the
+ * (lines per thread, CTA shape) on the plan's own buffers (two warm-up and
+ * five timed launches each, CUDA events on cuda_stream) and keep the
  * fastest.  Results are bit-identical across variants of a pass only up to
  * FP rounding order, which the variants share.  Synchronises cuda_stream;
  * allocates two temporary grid-sized buffers.  Errors: POISSON_ERR_ARG,

@@ -88,6 +88,18 @@ void free_plan(poisson_plan_s* p) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Tensor-core precisions run the z pass's radix-16 stages on tensor cores
+// where the z length is 16 M with M in {8, 16, 24, 32}; all other passes (and
+// other lengths) use the FP32 kernels.
+bool uses_tc(const poisson_plan_s* pl) {
+    return (pl->prec == POISSON_TC_FP16X2 || pl->prec == POISSON_TC_BF16X2) && z_tc_supported(pl->nz);
+}
+
+int variant_count(const poisson_plan_s* pl, int pass) {
+    if (pass == 2 && uses_tc(pl)) return 1;
+    return pass_variants(pl->prec == POISSON_FP64, pass);
+}
+
 template <class R>
 cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
     PassParams<R> p{};
@@ -106,8 +118,12 @@ cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void
         case 4: p.in = pl->w1; p.out = phi; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
         default: return cudaErrorInvalidValue;
     }
-    if constexpr (std::is_same<R, float>::value) return launch_pass_f32(N, pass, pl->var[pass], p, rows, st);
-    else return launch_pass_f64(N, pass, pl->var[pass], p, rows, st);
+    if constexpr (std::is_same<R, float>::value) {
+        if (pass == 2 && uses_tc(pl)) return launch_z_tc(N, pl->prec == POISSON_TC_BF16X2, p, st);
+        return launch_pass_f32(N, pass, pl->var[pass], p, rows, st);
+    } else {
+        return launch_pass_f64(N, pass, pl->var[pass], p, rows, st);
+    }
 }
 
 cudaError_t run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
@@ -115,14 +131,16 @@ cudaError_t run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* 
     return run_pass_t<float>(pl, pass, rho, phi, st);
 }
 
-// Default variant per pass before (or without) autotuning.
+// Default variant per pass before (or without) autotuning: the ones the
+// autotuner picks for 256^3 and 512^3 grids on GB300.
 int default_variant(poisson_precision prec, int pass) {
     if (prec == POISSON_FP64) return 0;
-    return (pass == 0 || pass == 4) ? 0 : 1;
+    static const int fp32_default[5] = {1, 0, 0, 2, 1};
+    return fp32_default[pass];
 }
 
 // Time every variant of every pass on the plan's own buffers and keep the
-// fastest (minimum of 3 timed launches after one warm-up launch each).
+// fastest (minimum of 5 timed launches after two warm-up launches each).
 poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
     const size_t cells = (size_t)pl->nx * pl->ny * pl->nz;
     void *rho = nullptr, *phi = nullptr;
@@ -138,14 +156,15 @@ poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
         if ((e = cudaEventCreate(&e0))) break;
         if ((e = cudaEventCreate(&e1))) break;
         for (int pass = 0; pass < 5 && e == cudaSuccess; ++pass) {
-            const int nv = pass_variants(pl->prec == POISSON_FP64, pass);
+            const int nv = variant_count(pl, pass);
             float best = 1e30f;
             int best_v = pl->var[pass];
             for (int v = 0; v < nv && e == cudaSuccess; ++v) {
                 pl->var[pass] = v;
                 if ((e = run_pass(pl, pass, rho, phi, st))) break;
+                if ((e = run_pass(pl, pass, rho, phi, st))) break;
                 float tmin = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < 5; ++rep) {
                     if ((e = cudaEventRecord(e0, st))) break;
                     if ((e = run_pass(pl, pass, rho, phi, st))) break;
                     if ((e = cudaEventRecord(e1, st))) break;
@@ -213,7 +232,8 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
         return POISSON_ERR_ARG;
     if (nx <= 0 || ny <= 0 || nz <= 0) return POISSON_ERR_ARG;
     if (!size_supported(nx) || !size_supported(ny) || !size_supported(nz)) return POISSON_ERR_UNSUPPORTED;
-    if (prec != POISSON_FP32 && prec != POISSON_FP64) return POISSON_ERR_UNSUPPORTED;
+    if (prec != POISSON_FP32 && prec != POISSON_FP64 && prec != POISSON_TC_FP16X2 && prec != POISSON_TC_BF16X2)
+        return POISSON_ERR_UNSUPPORTED;
     if (flags & ~(POISSON_FLAG_CHECK_FINITE | POISSON_FLAG_AUTOTUNE)) return POISSON_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
@@ -225,6 +245,7 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
     p->flags = flags;
     p->r_near = r_near;
     for (int pass = 0; pass < 5; ++pass) p->var[pass] = default_variant(prec, pass);
+    if (uses_tc(p)) p->var[2] = 0;
     if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return POISSON_ERR_CUDA; }
     p->rsize = prec == POISSON_FP64 ? 8 : 4;
     p->csize = 2 * p->rsize;
@@ -336,7 +357,7 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
     info->row_stride = plan->sx;
     for (int pass = 0; pass < 5; ++pass) {
         info->variant[pass] = plan->var[pass];
-        info->variant_count[pass] = pass_variants(plan->prec == POISSON_FP64, pass);
+        info->variant_count[pass] = variant_count(plan, pass);
     }
     return POISSON_OK;
 }
@@ -348,7 +369,7 @@ poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream) {
 
 poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant) {
     if (!plan || pass < 0 || pass > 4) return POISSON_ERR_ARG;
-    if (variant < 0 || variant >= pass_variants(plan->prec == POISSON_FP64, pass)) return POISSON_ERR_ARG;
+    if (variant < 0 || variant >= variant_count(plan, pass)) return POISSON_ERR_ARG;
     plan->var[pass] = variant;
     return POISSON_OK;
 }

@@ -47,8 +47,9 @@ inline bool size_supported(int n) {
 //   CTA threads; row passes (x forward, x inverse) likewise.
 template <class R> struct Variants;
 template <> struct Variants<float> {
-    using Col = std::tuple<Var<2, 128>, Var<2, 256>, Var<1, 256>, Var<1, 512>>;
-    using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>>;
+    using Col = std::tuple<Var<2, 128>, Var<2, 256>, Var<1, 256>, Var<1, 512>, Var<2, 64>,
+                           Var<2, 128, 3>, Var<2, 64, 5>>;
+    using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>, Var<1, 256, 3>>;
 };
 template <> struct Variants<double> {
     using Col = std::tuple<Var<1, 256>>;
@@ -74,7 +75,8 @@ cudaError_t launch_row_var(int var, int pass, const PassParams<typename C::R>& p
 template <class C, class Tuple, int I = 0>
 cudaError_t launch_col_var(int var, int pass, const PassParams<typename C::R>& p, cudaStream_t st) {
     if constexpr (I < (int)std::tuple_size<Tuple>::value) {
-        if (var == I) return launch_col<C, typename std::tuple_element<I, Tuple>::type>(pass, p, st);
+        using V = typename std::tuple_element<I, Tuple>::type;
+        if (var == I) return launch_col<C, V>(pass, p, st);
         return launch_col_var<C, Tuple, I + 1>(var, pass, p, st);
     } else {
         return cudaErrorInvalidValue;

@@ -28,6 +28,10 @@ cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz
 cudaError_t build_kernel_octant(int nx, int ny, int nz, double hx, double hy, double hz,
                                 int r_near, double* out, cudaStream_t st);
 
+// z pass with tensor-core radix-16 stages (split FP16 or BF16 operands)
+bool z_tc_supported(int N);
+cudaError_t launch_z_tc(int N, bool bf16, const PassParams<float>& p, cudaStream_t st);
+
 // DCT-I transform + scaling of a k(d) octant on caller-provided buffers
 // (no allocation, no synchronisation); see greens.cu.
 cudaError_t greens_transform_into(double* kbuf, double* tmp, const double* cx, const double* cy,

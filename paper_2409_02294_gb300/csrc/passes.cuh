@@ -100,6 +100,24 @@ inline int col_grid(int ncols, int L) {
 // to two thread groups (q = tid / (SLOTS T)) that meet through shared memory
 // for the final combine.
 
+// Exchange-buffer layout of a column tile: element i of a line lives in row
+// i (+ one padding row every 16 rows when a row is narrower than 128 bytes,
+// which spreads the stride-16 row patterns of the first Stockham stage over
+// all banks instead of one part of them).
+template <class R, int SLOTS> struct ColPad {
+    static constexpr bool on = SLOTS * (int)sizeof(cpx<R>) < 128;
+    static constexpr int shift = on ? 4 : 30;
+    static constexpr int pad = on ? SLOTS : 0;
+};
+template <class R, int N, int SLOTS> constexpr int col_rows() {
+    return N + (ColPad<R, SLOTS>::on ? N / 16 : 0);
+}
+template <class R, int N, int SLOTS>
+__device__ __forceinline__ LineSmem<R> col_line(cpx<R>* sm, int half, int slot) {
+    return {sm + half * col_rows<R, N, SLOTS>() * SLOTS + slot, SLOTS, ColPad<R, SLOTS>::shift,
+            ColPad<R, SLOTS>::pad};
+}
+
 template <class Cfg, int SLOTS, int LPT> struct ColIds {
     int slot, t, q;
     __device__ __forceinline__ ColIds() {
@@ -143,7 +161,7 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
     }
     LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = {sm + id.half(l) * N * SLOTS + id.slot, SLOTS, 30, 0};
+    for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
     line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
     if (c.valid) {
@@ -172,7 +190,7 @@ __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cf
         for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + cmulc(v[1][m], ldg_c(tw + id.t + T * m));
         return true;
     } else {
-        const LineSmem<R> lodd = {sm + N * SLOTS + id.slot, SLOTS, 30, 0};
+        const LineSmem<R> lodd = col_line<R, N, SLOTS>(sm, 1, id.slot);
         if (id.q) {
 #pragma unroll
             for (int m = 0; m < E; ++m) {
@@ -218,7 +236,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     }
     LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = {sm + id.half(l) * N * SLOTS + id.slot, SLOTS, 30, 0};
+    for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
     line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
     // Green's multiply at frequency (kx, ky, kz), folded into the octant.
@@ -273,7 +291,7 @@ __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p,
     }
     LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = {sm + id.half(l) * N * SLOTS + id.slot, SLOTS, 30, 0};
+    for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
     line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
     if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
@@ -386,26 +404,29 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
     // Z[2k'+1] = O[k'].
     cpx<R>* __restrict__ out = static_cast<cpx<R>*>(p.out);
     const long long sx = p.sx;
-    const int nout = nrows * (N + 1);
-    for (int i = threadIdx.x; i < nout; i += NT) {
-        const int s = i / (N + 1), k = i - s * (N + 1);
-        const int pp = s >> 1;
-        const int kh = k >> 1;
-        cpx<R> P, Q;
-        if ((k & 1) == 0) {
-            const LineSmem<R> e = {sm + pp * LS, 1, SH, 1};
-            P = e[kh];
-            Q = e[kh == 0 ? 0 : N - kh];
-        } else {
-            const LineSmem<R> o = {sm + (PAIRS + pp) * LS, 1, SH, 1};
-            P = o[kh];
-            Q = o[N - 1 - kh];
+    // each row pair is handled by the NT / PAIRS threads that share its pair
+    // index; one (P, Q) read gives both rows' bin k
+    constexpr int U = NT / PAIRS;
+    const int u = t + (LPT == 1 ? id.q * T : 0);
+    if (has_a) {
+        const LineSmem<R> e = {sm + pr * LS, 1, SH, 1};
+        const LineSmem<R> o = {sm + (PAIRS + pr) * LS, 1, SH, 1};
+        cpx<R>* ra = out + (long long)(r0 + 2 * pr) * sx;
+        cpx<R>* rb = ra + sx;
+        for (int k = u; k <= N; k += U) {
+            const int kh = k >> 1;
+            cpx<R> P, Q;
+            if ((k & 1) == 0) {
+                P = e[kh];
+                Q = e[kh == 0 ? 0 : N - kh];
+            } else {
+                P = o[kh];
+                Q = o[N - 1 - kh];
+            }
+            Q.y = -Q.y;
+            ra[k] = cpx<R>{(R)0.5 * (P.x + Q.x), (R)0.5 * (P.y + Q.y)};
+            if (has_b) rb[k] = cpx<R>{(R)0.5 * (P.y - Q.y), (R)(-0.5) * (P.x - Q.x)};
         }
-        Q.y = -Q.y;
-        cpx<R> r;
-        if ((s & 1) == 0) r = {(R)0.5 * (P.x + Q.x), (R)0.5 * (P.y + Q.y)};
-        else r = {(R)0.5 * (P.y - Q.y), (R)(-0.5) * (P.x - Q.x)};
-        out[(long long)(r0 + s) * sx + k] = r;
     }
 }
 
@@ -523,28 +544,28 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
 // ==========================================================================
 // kernels: one tile per CTA
 // ==========================================================================
-template <class Cfg, int SLOTS, int LPT>
-__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>()) k_y_fwd(PassParams<typename Cfg::R> p) {
+template <class Cfg, int SLOTS, int LPT, int MINB>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB) k_y_fwd(PassParams<typename Cfg::R> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile_y_fwd<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
 }
-template <class Cfg, int SLOTS, int LPT>
-__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>()) k_z_conv(PassParams<typename Cfg::R> p) {
+template <class Cfg, int SLOTS, int LPT, int MINB>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB) k_z_conv(PassParams<typename Cfg::R> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile_z_conv<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
 }
-template <class Cfg, int SLOTS, int LPT>
-__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>()) k_y_inv(PassParams<typename Cfg::R> p) {
+template <class Cfg, int SLOTS, int LPT, int MINB>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB) k_y_inv(PassParams<typename Cfg::R> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile_y_inv<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
 }
-template <class Cfg, int PAIRS, int LPT>
-__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>()) k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
+template <class Cfg, int PAIRS, int LPT, int MINB>
+__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>(), MINB) k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile_x_fwd<Cfg, PAIRS, LPT, false>(p, rows, blockIdx.x, smem_raw);
 }
-template <class Cfg, int PAIRS, int LPT>
-__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>()) k_x_inv(PassParams<typename Cfg::R> p, int rows) {
+template <class Cfg, int PAIRS, int LPT, int MINB>
+__global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>(), MINB) k_x_inv(PassParams<typename Cfg::R> p, int rows) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile_x_inv<Cfg, PAIRS, LPT, false>(p, rows, blockIdx.x, smem_raw);
 }
@@ -572,14 +593,15 @@ template <int PASS, class Cfg, int A, int B> struct SmemTag {};
 // A variant fixes lines per thread and the CTA's target thread count; the
 // tile width (column passes: SLOTS lines, row passes: PAIRS row pairs)
 // follows from the line's thread count T.
-template <int LPT_, int THREADS_> struct Var {
+template <int LPT_, int THREADS_, int MINB_ = 1> struct Var {
     static constexpr int LPT = LPT_;
     static constexpr int THREADS = THREADS_;
+    static constexpr int MINB = MINB_;  // minimum resident CTAs per SM (register cap)
 };
 
 template <class Cfg, class V> constexpr int var_slots() {
     constexpr int XW = Seg<typename Cfg::R>::XW;
-    constexpr int lo = XW / 2 < 8 ? 8 : XW / 2;           // >= 64-byte row segments
+    constexpr int lo = XW / 4;  // >= 32-byte row segments
     constexpr int s = V::THREADS / ((V::LPT == 1 ? 2 : 1) * Cfg::T);
     return s < lo ? lo : s;
 }
@@ -588,7 +610,7 @@ template <class Cfg, class V> constexpr int var_pairs() {
     return s < 1 ? 1 : s;
 }
 template <class Cfg, int SLOTS> constexpr size_t col_smem() {
-    return 2ull * Cfg::N * SLOTS * sizeof(cpx<typename Cfg::R>);
+    return 2ull * col_rows<typename Cfg::R, Cfg::N, SLOTS>() * SLOTS * sizeof(cpx<typename Cfg::R>);
 }
 template <class Cfg, int PAIRS> constexpr size_t row_smem() {
     using R = typename Cfg::R;
@@ -611,11 +633,11 @@ cudaError_t launch_row(int pass, const PassParams<typename Cfg::R>& p, int rows,
     if (grid == 0) return cudaSuccess;
     cudaError_t e;
     if (pass == 0) {
-        if ((e = set_smem<SmemTag<0, Cfg, P, L>>(k_x_fwd<Cfg, P, L>, sm)) != cudaSuccess) return e;
-        k_x_fwd<Cfg, P, L><<<grid, NT, sm, st>>>(p, rows);
+        if ((e = set_smem<SmemTag<0, Cfg, P, L * 16 + V::MINB>>(k_x_fwd<Cfg, P, L, V::MINB>, sm)) != cudaSuccess) return e;
+        k_x_fwd<Cfg, P, L, V::MINB><<<grid, NT, sm, st>>>(p, rows);
     } else {
-        if ((e = set_smem<SmemTag<4, Cfg, P, L>>(k_x_inv<Cfg, P, L>, sm)) != cudaSuccess) return e;
-        k_x_inv<Cfg, P, L><<<grid, NT, sm, st>>>(p, rows);
+        if ((e = set_smem<SmemTag<4, Cfg, P, L * 16 + V::MINB>>(k_x_inv<Cfg, P, L, V::MINB>, sm)) != cudaSuccess) return e;
+        k_x_inv<Cfg, P, L, V::MINB><<<grid, NT, sm, st>>>(p, rows);
     }
     return cudaGetLastError();
 }
@@ -633,14 +655,14 @@ cudaError_t launch_col(int pass, const PassParams<typename Cfg::R>& p, cudaStrea
     if (grid == 0) return cudaSuccess;
     cudaError_t e;
     if (pass == 1) {
-        if ((e = set_smem<SmemTag<1, Cfg, S, L>>(k_y_fwd<Cfg, S, L>, sm)) != cudaSuccess) return e;
-        k_y_fwd<Cfg, S, L><<<grid, NT, sm, st>>>(p);
+        if ((e = set_smem<SmemTag<1, Cfg, S, L * 16 + V::MINB>>(k_y_fwd<Cfg, S, L, V::MINB>, sm)) != cudaSuccess) return e;
+        k_y_fwd<Cfg, S, L, V::MINB><<<grid, NT, sm, st>>>(p);
     } else if (pass == 3) {
-        if ((e = set_smem<SmemTag<3, Cfg, S, L>>(k_y_inv<Cfg, S, L>, sm)) != cudaSuccess) return e;
-        k_y_inv<Cfg, S, L><<<grid, NT, sm, st>>>(p);
+        if ((e = set_smem<SmemTag<3, Cfg, S, L * 16 + V::MINB>>(k_y_inv<Cfg, S, L, V::MINB>, sm)) != cudaSuccess) return e;
+        k_y_inv<Cfg, S, L, V::MINB><<<grid, NT, sm, st>>>(p);
     } else {
-        if ((e = set_smem<SmemTag<2, Cfg, S, L>>(k_z_conv<Cfg, S, L>, sm)) != cudaSuccess) return e;
-        k_z_conv<Cfg, S, L><<<grid, NT, sm, st>>>(p);
+        if ((e = set_smem<SmemTag<2, Cfg, S, L * 16 + V::MINB>>(k_z_conv<Cfg, S, L, V::MINB>, sm)) != cudaSuccess) return e;
+        k_z_conv<Cfg, S, L, V::MINB><<<grid, NT, sm, st>>>(p);
     }
     return cudaGetLastError();
 }
