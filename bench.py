@@ -206,6 +206,30 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(value, world, device=None):
+    """Largest `value` over all ranks (the job's wall time is the slowest
+    rank's); identity on one rank.  Works with any torch.distributed backend
+    (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, cells_per_rank, steps, max_seconds):
+    """Whole-job throughput: every rank solves its own field each step, so
+    the job solves world * cells_per_rank cells per step."""
+    return world * cells_per_rank * steps / max_seconds
+
+
+def field_seed(base_seed, rank, nfields, field):
+    """Seed of field `field` of `rank`: every rank's fields are distinct."""
+    return base_seed + rank * nfields + field
+
+
 def library_baselines(plan, rho, n, steps, flush, stream):
     """cuFFT (through torch.fft) timed on the same GPU as library baselines:
     (a) 3-D R2C/C2R with separate pad, multiply and crop kernels, and
@@ -379,7 +403,7 @@ def run_ours(args):
     wl = args.workload
     n = WORKLOADS[wl]["n"]
     nf = WORKLOADS[wl].get("fields", 1)
-    rhos32 = [make_density(wl, args.seed + rank * nf + i) for i in range(nf)]
+    rhos32 = [make_density(wl, field_seed(args.seed, rank, nf, i)) for i in range(nf)]
     rho32 = rhos32[0]
     rhos = [torch.from_numpy(r).to(dev) for r in rhos32]
     phis = [torch.empty_like(r) for r in rhos]
@@ -388,10 +412,17 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(evs=None):
+    fused = plan.info()["fused"]
+
+    def step(evs=None, per_pass=False):
         for f in range(nf):
             if evs is not None and f == 0:
                 evs[0].record(stream)
+            if fused and not per_pass:
+                plan.solve(rhos[f], out=phis[f], stream=stream)
+                if evs is not None:
+                    evs[f * 5 + 5].record(stream)
+                continue
             for i in range(5):
                 plan.solve_pass(i, rhos[f], phis[f], stream)
                 if evs is not None:
@@ -419,15 +450,23 @@ def run_ours(args):
     clocks = sampler.stop()
 
     step_ms = [ev[0].elapsed_time(ev[5 * nf]) for ev in events]
-    pass_ms = [sum(ev[f * 5 + i].elapsed_time(ev[f * 5 + i + 1]) for ev in events for f in range(nf))
-               / (args.steps * nf) for i in range(5)]
+    if fused:
+        # per-pass breakdown of the five-launch mode, measured after the timed
+        # region, for the roofline of each kernel
+        pev = [[torch.cuda.Event(enable_timing=True) for _ in range(5 * nf + 1)]
+               for _ in range(min(args.steps, 50))]
+        for ev in pev:
+            flush.zero_()
+            step(ev, per_pass=True)
+        torch.cuda.synchronize()
+    else:
+        pev = events
+    pass_ms = [sum(ev[f * 5 + i].elapsed_time(ev[f * 5 + i + 1]) for ev in pev for f in range(nf))
+               / (len(pev) * nf) for i in range(5)]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     cells = n ** 3 * nf
-    value = world * cells * args.steps / (total_ms / 1e3)
+    value = weak_scaling_value(world, cells, args.steps, total_ms / 1e3)
 
     # accuracy of this run's output against the FP64 oracle, and the oracle
     # timed on the host cores (rank 0, N = 1 only)
@@ -473,11 +512,8 @@ def run_ours(args):
         for _ in range(ksteps):
             plan.solve_host(host_in, host_out, stream)
         te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * n ** 3 * ksteps / te, "unit": UNIT,
+        te = max_over_ranks(te, world, dev)
+        e2e = {"value": weak_scaling_value(world, n ** 3, ksteps, te), "unit": UNIT,
                "h2d_bytes_per_step": rho32.nbytes, "d2h_bytes_per_step": rho32.nbytes,
                "steps": ksteps, "host_memory": "pinned"}
         if rank == 0 and world == 1:
@@ -495,8 +531,16 @@ def run_ours(args):
         KERNEL_NAMES[2] = "k_z_conv_tc"
     pb = pass_bytes(n, n, n)
     peak, peak_kind = peaks()
-    achieved = pb[dom] / (pass_ms[dom] / 1e3) / 1e9
-    traffic = profiled_traffic(KERNEL_NAMES[dom], wl)
+    if fused:
+        # the whole solve is one kernel: its algorithmic bytes are all passes'
+        dom_name = "k_fused"
+        dom_bytes = sum(pb)
+        achieved = dom_bytes * nf / (total_ms / args.steps / 1e3) / 1e9
+    else:
+        dom_name = KERNEL_NAMES[dom]
+        dom_bytes = pb[dom]
+        achieved = pb[dom] / (pass_ms[dom] / 1e3) / 1e9
+    traffic = profiled_traffic(dom_name, wl)
 
     if rank == 0:
         line = {
@@ -508,21 +552,24 @@ def run_ours(args):
             "config": {"workload": wl, "description": WORKLOADS[wl]["desc"], "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": "independent field per GPU" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                          if peak_kind == "measured" else "fallback 6800 GB/s",
-                         "traffic": traffic, "algorithmic_bytes": pb[dom]},
-            "passes": {PASS_NAMES[i]: {"ms": pass_ms[i], "GBps": pb[i] / (pass_ms[i] / 1e3) / 1e9,
+                         "traffic": traffic, "algorithmic_bytes": dom_bytes},
+            "execution": "one persistent dataflow kernel per solve (mode %d)" % fused if fused
+                         else "five kernel launches per solve",
+            "passes" if not fused else "five_launch_breakdown":
+                {PASS_NAMES[i]: {"ms": pass_ms[i], "GBps": pb[i] / (pass_ms[i] / 1e3) / 1e9,
                                        "frac": pb[i] / (pass_ms[i] / 1e3) / 1e9 / peak}
                        for i in range(5)},
-            "solve_roofline_frac": sum(pb) / (sum(pass_ms) / 1e3) / 1e9 / peak,
+            "solve_roofline_frac": sum(pb) * nf / (total_ms / args.steps / 1e3) / 1e9 / peak,
             "accuracy": acc,
             "library_baselines_same_gpu": libs,
             "host_transfer_128cube_fp64": host_xfer,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 5 * nf * args.steps,
+            "gpu_launches": (1 if fused else 5) * nf * args.steps,
             "kernel_variants": plan.info()["variant"],
             "clocks": clocks,
             "wall_s_timed": t_wall,

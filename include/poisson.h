@@ -160,6 +160,7 @@ typedef struct {
     long long row_stride;    /* complex elements per work-buffer row */
     int variant[5];          /* kernel variant in use per pass */
     int variant_count[5];    /* variants available per pass */
+    int fused;               /* 0: five launches per solve; 1, 2: one persistent dataflow kernel */
 } poisson_plan_info;
 
 /* Fill *info.  Errors: POISSON_ERR_ARG. */
@@ -169,15 +170,21 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
  * Autotuner: for each of the five passes, time every compiled kernel variant
  * (lines per thread, CTA shape) on the plan's own buffers (two warm-up and
  * five timed launches each, CUDA events on cuda_stream) and keep the
- * fastest.  Results are bit-identical across variants of a pass only up to
- * FP rounding order, which the variants share.  Synchronises cuda_stream;
+ * fastest, then (cubic FP32 grids) times five launches against the fused
+ * persistent kernel and keeps the faster mode.  Synchronises cuda_stream;
  * allocates two temporary grid-sized buffers.  Errors: POISSON_ERR_ARG,
  * POISSON_ERR_ALLOC, POISSON_ERR_CUDA.
  */
 poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream);
 
 /* Select kernel variant `variant` for `pass` (0..4) explicitly (for tests
- * and experiments).  Errors: POISSON_ERR_ARG (out of range). */
+ * and experiments).  pass = 5 selects the execution mode: 0 = five kernel
+ * launches per solve, 1 or 2 = one persistent kernel that overlaps the
+ * passes through tile-level dependencies, compiled for 3 or 2 resident CTAs
+ * per SM (cubic FP32 grids of edge 64, 128, 192,
+ * 256, 384 or 512; otherwise POISSON_ERR_UNSUPPORTED).  The autotuner picks
+ * the faster mode where both exist.  Errors: POISSON_ERR_ARG (out of range),
+ * POISSON_ERR_UNSUPPORTED, POISSON_ERR_CUDA. */
 poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant);
 
 /*

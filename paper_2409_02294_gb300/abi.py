@@ -36,6 +36,7 @@ class PlanInfo(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t), ("greens_bytes", ctypes.c_size_t),
         ("row_stride", ctypes.c_longlong),
         ("variant", ctypes.c_int * 5), ("variant_count", ctypes.c_int * 5),
+        ("fused", ctypes.c_int),
     ]
 
 

@@ -83,6 +83,8 @@ void free_plan(poisson_plan_s* p) {
     cudaFree(p->status);
     cudaFree(p->stage_in);
     cudaFree(p->stage_out);
+    cudaFree(p->fused_order);
+    cudaFree(p->fused_ctl);
     delete p;
 }
 
@@ -101,7 +103,7 @@ int variant_count(const poisson_plan_s* pl, int pass) {
 }
 
 template <class R>
-cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
+PassParams<R> pass_params_t(const poisson_plan_s* pl, int pass, const void* rho, void* phi, int& N) {
     PassParams<R> p{};
     p.nx = pl->nx;
     p.ny = pl->ny;
@@ -109,15 +111,22 @@ cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void
     p.sx = pl->sx;
     p.status = pl->status;
     p.greens = static_cast<const R*>(pl->greens);
-    int N = 0, rows = pl->ny * pl->nz;
     switch (pass) {
         case 0: p.in = rho; p.out = pl->w1; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
         case 1: p.in = pl->w1; p.out = pl->w2; N = pl->ny; p.tw = static_cast<const cpx<R>*>(pl->tw[1]); break;
         case 2: p.in = pl->w2; p.out = pl->w2; N = pl->nz; p.tw = static_cast<const cpx<R>*>(pl->tw[2]); break;
         case 3: p.in = pl->w2; p.out = pl->w1; N = pl->ny; p.tw = static_cast<const cpx<R>*>(pl->tw[1]); break;
-        case 4: p.in = pl->w1; p.out = phi; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
-        default: return cudaErrorInvalidValue;
+        default: p.in = pl->w1; p.out = phi; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
     }
+    return p;
+}
+
+template <class R>
+cudaError_t run_pass_t(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
+    if (pass < 0 || pass > 4) return cudaErrorInvalidValue;
+    int N = 0;
+    const int rows = pl->ny * pl->nz;
+    const PassParams<R> p = pass_params_t<R>(pl, pass, rho, phi, N);
     if constexpr (std::is_same<R, float>::value) {
         if (pass == 2 && uses_tc(pl)) return launch_z_tc(N, pl->prec == POISSON_TC_BF16X2, p, st);
         return launch_pass_f32(N, pass, pl->var[pass], p, rows, st);
@@ -130,6 +139,8 @@ cudaError_t run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* 
     if (pl->prec == POISSON_FP64) return run_pass_t<double>(pl, pass, rho, phi, st);
     return run_pass_t<float>(pl, pass, rho, phi, st);
 }
+
+poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStream_t st);
 
 // Default variant per pass before (or without) autotuning: the ones the
 // autotuner picks for 256^3 and 512^3 grids on GB300.
@@ -177,6 +188,27 @@ poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
             }
             pl->var[pass] = best_v;
         }
+        // execution mode: five launches or the fused dataflow kernel
+        if (e == cudaSuccess && fused_supported(pl)) {
+            if ((e = fused_prepare(pl, st))) break;
+            float best[3] = {1e30f, 1e30f, 1e30f};
+            for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+                pl->use_fused = mode;
+                for (int rep = 0; rep < 6; ++rep) {
+                    if ((e = cudaEventRecord(e0, st))) break;
+                    if (solve_all(pl, rho, phi, st) != POISSON_OK) { e = cudaErrorUnknown; break; }
+                    if ((e = cudaEventRecord(e1, st))) break;
+                    if ((e = cudaEventSynchronize(e1))) break;
+                    float ms = 0.f;
+                    if ((e = cudaEventElapsedTime(&ms, e0, e1))) break;
+                    if (rep >= 1) best[mode] = ms < best[mode] ? ms : best[mode];
+                }
+            }
+            int bm = 0;
+            for (int mode = 1; mode < 3; ++mode)
+                if (best[mode] < best[bm]) bm = mode;
+            pl->use_fused = bm;
+        }
     } while (0);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -195,6 +227,12 @@ poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStr
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) {
         if (cudaSetDevice(plan->device) != cudaSuccess) return POISSON_ERR_CUDA;
+    }
+    if (plan->use_fused) {
+        PassParams<float> p[5];
+        int N = 0;
+        for (int pass = 0; pass < 5; ++pass) p[pass] = pass_params_t<float>(plan, pass, in, out, N);
+        return cuda_status(fused_solve(plan, p, st));
     }
     for (int pass = 0; pass < 5; ++pass) {
         cudaError_t e = run_pass(plan, pass, in, out, st);
@@ -359,6 +397,7 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
         info->variant[pass] = plan->var[pass];
         info->variant_count[pass] = variant_count(plan, pass);
     }
+    info->fused = plan->use_fused;
     return POISSON_OK;
 }
 
@@ -368,7 +407,17 @@ poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream) {
 }
 
 poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant) {
-    if (!plan || pass < 0 || pass > 4) return POISSON_ERR_ARG;
+    if (!plan || pass < 0 || pass > 5) return POISSON_ERR_ARG;
+    if (pass == 5) {
+        if (variant < 0 || variant > 2) return POISSON_ERR_ARG;
+        if (variant > 0) {
+            if (!fused_supported(plan)) return POISSON_ERR_UNSUPPORTED;
+            cudaError_t e = fused_prepare(plan, nullptr);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        plan->use_fused = variant;
+        return POISSON_OK;
+    }
     if (variant < 0 || variant >= variant_count(plan, pass)) return POISSON_ERR_ARG;
     plan->var[pass] = variant;
     return POISSON_OK;

@@ -13,9 +13,9 @@
 // that makes every other CTA stop, and the kernel returns.
 //
 // Data produced inside the launch is read with L1-bypassing loads (the tile
-// functions' CG = true instantiation); completion is published with a
-// device-scope fence before the counter increment and observed with an
-// acquire load.
+// functions' CG = true instantiation); completion is published by one
+// thread with a device-scope fence after the CTA barrier and before the
+// counter increment, and observed with an acquire load.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -137,9 +137,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched(BatchArgs a) {
             case 384: batch_tile<384>(sg.pass, p, f.rows, tile, smem_raw); break;
             default: batch_tile<512>(sg.pass, p, f.rows, tile, smem_raw); break;
         }
-        __threadfence();  // this thread's stores are visible GPU-wide ...
-        __syncthreads();  // ... for every thread of the tile ...
-        if (threadIdx.x == 0) atomicAdd(a.ctl + 2 + sg.field * 5 + sg.pass, 1u);  // ... before the count
+        // release: the barrier orders every thread's stores before thread 0's
+        // device-scope fence, which orders them before the count update
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.ctl + 2 + sg.field * 5 + sg.pass, 1u);
+        }
     }
 }
 

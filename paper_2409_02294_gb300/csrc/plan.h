@@ -24,12 +24,22 @@ struct poisson_plan_s {
     void* stage_in;       // device staging for poisson_solve_host
     void* stage_out;
     int var[5];           // kernel variant per pass (autotuned or default)
+    int use_fused;        // 1: one persistent dataflow kernel instead of five launches
+    void* fused_order;    // its work queue ((pass, tile) pairs) and counters
+    void* fused_ctl;
+    int fused_total;
+    int fused_ctl_words;
 };
 
 namespace pgb {
 // Drop every cached batched-solve graph that refers to `plan` (called when
 // the plan is destroyed).
 void batch_forget_plan(poisson_plan_t plan);
+// Single-field fused dataflow solve (fused.cu).
+template <class R> struct PassParams;
+bool fused_supported(const poisson_plan_s* pl);
+cudaError_t fused_prepare(poisson_plan_s* pl, cudaStream_t st);
+cudaError_t fused_solve(const poisson_plan_s* pl, const PassParams<float> (&p)[5], cudaStream_t st);
 // The batched solve (poisson_solve_batched after argument checks).
 poisson_status batched_solve(poisson_plan_t const* plans, int count, const void* const* rho,
                              void* const* phi, cudaStream_t st);

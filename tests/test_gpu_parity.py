@@ -321,3 +321,31 @@ def test_autotuned_plan_matches_oracle(pg, oracle_mod):
     for o in (out, out2):
         l2, mx = rel_errors(o, ref)
         assert l2 <= TOL32[0] and mx <= TOL32[1]
+
+
+# ---------------------------------------------------------------------------
+# fused single-field dataflow kernel
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [64, 128, 192, 256])
+def test_fused_dataflow_solve_matches_oracle(pg, oracle_mod, n):
+    rho = np.random.default_rng(n).standard_normal((n, n, n)).astype(np.float32)
+    ref = oracle_mod.solve_fft(rho.astype(np.float64))
+    x = torch.from_numpy(rho).cuda()
+    with pg.Plan(n) as plan:
+        five = plan.solve(x).double().cpu().numpy()
+        for mode in (1, 2):
+            plan.set_variant(5, mode)
+            assert plan.info()["fused"] == mode
+            for _ in range(2):  # repeated launches reuse the counters
+                out = plan.solve(x).double().cpu().numpy()
+                l2, mx = rel_errors(out, ref)
+                assert l2 <= TOL32[0] and mx <= TOL32[1], (mode, l2, mx)
+            assert plan.sync_status() == 0
+        assert np.abs(out - five).max() <= 1e-6 * np.abs(five).max()
+
+
+def test_fused_mode_rejected_for_unsupported_shapes(pg):
+    with pg.Plan(64, 32, 32) as plan:
+        with pytest.raises(pg.PoissonError):
+            plan.set_variant(5, 1)
