@@ -160,7 +160,7 @@ typedef struct {
     long long row_stride;    /* complex elements per work-buffer row */
     int variant[5];          /* kernel variant in use per pass */
     int variant_count[5];    /* variants available per pass */
-    int fused;               /* 0: five launches per solve; 1, 2: one persistent dataflow kernel */
+    int fused;               /* execution mode: 0 five launches, 1-2 fused kernel, 3-4 banded */
 } poisson_plan_info;
 
 /* Fill *info.  Errors: POISSON_ERR_ARG. */
@@ -181,9 +181,11 @@ poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream);
  * and experiments).  pass = 5 selects the execution mode: 0 = five kernel
  * launches per solve, 1 or 2 = one persistent kernel that overlaps the
  * passes through tile-level dependencies, compiled for 3 or 2 resident CTAs
- * per SM (cubic FP32 grids of edge 64, 128, 192,
- * 256, 384 or 512; otherwise POISSON_ERR_UNSUPPORTED).  The autotuner picks
- * the faster mode where both exist.  Errors: POISSON_ERR_ARG (out of range),
+ * per SM (cubic FP32 grids of edge 64, 128, 192, 256, 384 or 512), 3 or 4 =
+ * "banded": the column passes of 4 or 8 bands of kx columns run as staggered
+ * chains on plan-owned streams forked from and joined back to cuda_stream
+ * (FP32 plans); unsupported combinations return POISSON_ERR_UNSUPPORTED.
+ * The autotuner picks the fastest mode available.  Errors: POISSON_ERR_ARG (out of range),
  * POISSON_ERR_UNSUPPORTED, POISSON_ERR_CUDA. */
 poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant);
 

@@ -85,6 +85,14 @@ void free_plan(poisson_plan_s* p) {
     cudaFree(p->stage_out);
     cudaFree(p->fused_order);
     cudaFree(p->fused_ctl);
+    if (p->band_ready) {
+        for (int k = 0; k < 8; ++k) {
+            cudaStreamDestroy(p->band_stream[k]);
+            cudaEventDestroy(p->band_ev_y[k]);
+            cudaEventDestroy(p->band_ev_done[k]);
+        }
+        cudaEventDestroy(p->band_ev_x);
+    }
     delete p;
 }
 
@@ -141,6 +149,7 @@ cudaError_t run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* 
 }
 
 poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStream_t st);
+bool banded_supported(const poisson_plan_s* pl);
 
 // Default variant per pass before (or without) autotuning: the ones the
 // autotuner picks for 256^3 and 512^3 grids on GB300.
@@ -188,11 +197,14 @@ poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
             }
             pl->var[pass] = best_v;
         }
-        // execution mode: five launches or the fused dataflow kernel
-        if (e == cudaSuccess && fused_supported(pl)) {
-            if ((e = fused_prepare(pl, st))) break;
-            float best[3] = {1e30f, 1e30f, 1e30f};
-            for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+        // execution mode: five launches, the fused dataflow kernel (1, 2) or
+        // banded streams (3, 4)
+        if (e == cudaSuccess && (fused_supported(pl) || banded_supported(pl))) {
+            if (fused_supported(pl) && (e = fused_prepare(pl, st))) break;
+            float best[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+            for (int mode = 0; mode < 5 && e == cudaSuccess; ++mode) {
+                if ((mode == 1 || mode == 2) && !fused_supported(pl)) continue;
+                if (mode >= 3 && !banded_supported(pl)) continue;
                 pl->use_fused = mode;
                 for (int rep = 0; rep < 6; ++rep) {
                     if ((e = cudaEventRecord(e0, st))) break;
@@ -205,7 +217,7 @@ poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
                 }
             }
             int bm = 0;
-            for (int mode = 1; mode < 3; ++mode)
+            for (int mode = 1; mode < 5; ++mode)
                 if (best[mode] < best[bm]) bm = mode;
             pl->use_fused = bm;
         }
@@ -223,11 +235,81 @@ poisson_status check_io(poisson_plan_t plan, const void* in, const void* out) {
     return POISSON_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Banded execution: the column passes (y forward, z, y inverse) of each band
+// of kx columns run as a chain on their own stream, band k's y forward
+// starting after band k-1's, so the arithmetic-bound z kernel of one band
+// shares the SMs with the memory-bound y kernels of its neighbours.  The x
+// passes cover all columns and stay on the caller's stream (fork after x
+// forward, join before x inverse).
+// ---------------------------------------------------------------------------
+int band_count(int mode) { return mode == 3 ? 4 : 8; }
+bool banded_supported(const poisson_plan_s* pl) { return pl->prec == POISSON_FP32; }
+
+cudaError_t band_prepare(poisson_plan_s* pl) {
+    if (pl->band_ready) return cudaSuccess;
+    cudaError_t e;
+    for (int k = 0; k < 8; ++k) {
+        if ((e = cudaStreamCreateWithFlags(&pl->band_stream[k], cudaStreamNonBlocking))) return e;
+        if ((e = cudaEventCreateWithFlags(&pl->band_ev_y[k], cudaEventDisableTiming))) return e;
+        if ((e = cudaEventCreateWithFlags(&pl->band_ev_done[k], cudaEventDisableTiming))) return e;
+    }
+    if ((e = cudaEventCreateWithFlags(&pl->band_ev_x, cudaEventDisableTiming))) return e;
+    pl->band_ready = true;
+    return cudaSuccess;
+}
+
+// tile range of band k (of nb) for column pass `pass` with its current variant
+void band_range(const poisson_plan_s* pl, int pass, int k, int nb, int& tile0, int& ntile) {
+    const int N = pass == 2 ? pl->nz : pl->ny;
+    const int S = col_slots_for<float>(N, pl->var[pass]);
+    const int XW = S < 16 ? S : 16, NLW = S / XW;
+    const int ncols = pl->nx + 1, L = pass == 2 ? 2 * pl->ny : pl->nz;
+    const int nxw = ncols / XW, nlt = (L + NLW - 1) / NLW;
+    const int nleft = ncols - nxw * XW;
+    const int total = nxw * nlt + nleft * ((L + S - 1) / S);
+    const int G = ncols / 16;  // whole 16-column groups (band boundaries)
+    const int c0 = (k * G / nb) * 16 / XW;
+    const int c1 = k == nb - 1 ? nxw : ((k + 1) * G / nb) * 16 / XW;
+    tile0 = c0 * nlt;
+    ntile = (k == nb - 1 ? total : c1 * nlt) - tile0;
+}
+
+poisson_status solve_banded(poisson_plan_s* pl, const void* in, void* out, cudaStream_t st) {
+    const int nb = band_count(pl->use_fused);
+    cudaError_t e;
+    if ((e = band_prepare(pl))) return cuda_status(e);
+    if ((e = run_pass(pl, 0, in, out, st))) return cuda_status(e);
+    if ((e = cudaEventRecord(pl->band_ev_x, st))) return cuda_status(e);
+    const int rows = pl->ny * pl->nz;
+    for (int k = 0; k < nb; ++k) {
+        cudaStream_t bs = pl->band_stream[k];
+        if ((e = cudaStreamWaitEvent(bs, pl->band_ev_x, 0))) return cuda_status(e);
+        if (k > 0 && (e = cudaStreamWaitEvent(bs, pl->band_ev_y[k - 1], 0))) return cuda_status(e);
+        for (int pass = 1; pass <= 3; ++pass) {
+            int N = 0, t0 = 0, nt = 0;
+            PassParams<float> p = pass_params_t<float>(pl, pass, in, out, N);
+            band_range(pl, pass, k, nb, t0, nt);
+            if (nt > 0) {
+                p.tile0 = t0;
+                p.ntile = nt;
+                if ((e = launch_pass_f32(N, pass, pl->var[pass], p, rows, bs))) return cuda_status(e);
+            }
+            if (pass == 1 && (e = cudaEventRecord(pl->band_ev_y[k], bs))) return cuda_status(e);
+        }
+        if ((e = cudaEventRecord(pl->band_ev_done[k], bs))) return cuda_status(e);
+    }
+    for (int k = 0; k < nb; ++k)
+        if ((e = cudaStreamWaitEvent(st, pl->band_ev_done[k], 0))) return cuda_status(e);
+    return cuda_status(run_pass(pl, 4, in, out, st));
+}
+
 poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStream_t st) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) {
         if (cudaSetDevice(plan->device) != cudaSuccess) return POISSON_ERR_CUDA;
     }
+    if (plan->use_fused >= 3) return solve_banded(plan, in, out, st);
     if (plan->use_fused) {
         PassParams<float> p[5];
         int N = 0;
@@ -409,8 +491,10 @@ poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream) {
 poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant) {
     if (!plan || pass < 0 || pass > 5) return POISSON_ERR_ARG;
     if (pass == 5) {
-        if (variant < 0 || variant > 2) return POISSON_ERR_ARG;
-        if (variant > 0) {
+        if (variant < 0 || variant > 4) return POISSON_ERR_ARG;
+        if (variant >= 3) {
+            if (!banded_supported(plan)) return POISSON_ERR_UNSUPPORTED;
+        } else if (variant > 0) {
             if (!fused_supported(plan)) return POISSON_ERR_UNSUPPORTED;
             cudaError_t e = fused_prepare(plan, nullptr);
             if (e != cudaSuccess) return cuda_status(e);

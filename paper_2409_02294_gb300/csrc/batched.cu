@@ -59,7 +59,7 @@ template <int N> struct BatchShape {
     static constexpr int P = var_pairs<C, BatchVar>();
     static_assert(col_threads<C, S, 1>() == BATCH_THREADS, "column tile must use 256 threads");
     static_assert(row_threads<C, P, 1>() == BATCH_THREADS, "row tile must use 256 threads");
-    static constexpr size_t smem = col_smem<C, S>() > row_smem<C, P>() ? col_smem<C, S>() : row_smem<C, P>();
+    static constexpr size_t smem = col_smem_z<C, S>() > row_smem<C, P>() ? col_smem_z<C, S>() : row_smem<C, P>();
 };
 
 template <int N>

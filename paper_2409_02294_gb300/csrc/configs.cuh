@@ -83,6 +83,32 @@ cudaError_t launch_col_var(int var, int pass, const PassParams<typename C::R>& p
     }
 }
 
+// Tile width (SLOTS) of column variant `var` for transform length N (host).
+template <class R, int N, class Tuple, int I = 0> int col_slots_var(int var) {
+    if constexpr (I < (int)std::tuple_size<Tuple>::value) {
+        if (var == I) return var_slots<typename SizeCfg<R, N>::C, typename std::tuple_element<I, Tuple>::type>();
+        return col_slots_var<R, N, Tuple, I + 1>(var);
+    } else {
+        return 0;
+    }
+}
+template <class R> int col_slots_for(int N, int var) {
+    using T = typename Variants<R>::Col;
+    switch (N) {
+        case 16: return col_slots_var<R, 16, T>(var);
+        case 32: return col_slots_var<R, 32, T>(var);
+        case 48: return col_slots_var<R, 48, T>(var);
+        case 64: return col_slots_var<R, 64, T>(var);
+        case 96: return col_slots_var<R, 96, T>(var);
+        case 128: return col_slots_var<R, 128, T>(var);
+        case 192: return col_slots_var<R, 192, T>(var);
+        case 256: return col_slots_var<R, 256, T>(var);
+        case 384: return col_slots_var<R, 384, T>(var);
+        case 512: return col_slots_var<R, 512, T>(var);
+        default: return 0;
+    }
+}
+
 // Dispatch one pass of group GROUP for edge length N (the pass's axis).
 template <class R, int GROUP, int N>
 cudaError_t launch_group_n(int pass, int var, const PassParams<R>& p, int rows, cudaStream_t st) {

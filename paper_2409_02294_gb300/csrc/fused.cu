@@ -42,7 +42,7 @@ template <int N> struct FusedShape {
     static constexpr int NLW = S / XW;
     static_assert(col_threads<C, S, L>() == FUSED_THREADS, "column tile must use 128 threads");
     static_assert(row_threads<C, P, L>() == FUSED_THREADS, "row tile must use 128 threads");
-    static constexpr size_t smem = col_smem<C, S>() > row_smem<C, P>() ? col_smem<C, S>() : row_smem<C, P>();
+    static constexpr size_t smem = col_smem_z<C, S>() > row_smem<C, P>() ? col_smem_z<C, S>() : row_smem<C, P>();
 };
 
 struct FusedArgs {
@@ -88,13 +88,14 @@ __device__ __forceinline__ void col_tile_span(int tile, int L, int& chunk, int& 
     const int nxw = ncols / F::XW;
     const int n_wide = nxw * ((L + F::NLW - 1) / F::NLW);
     if (tile < n_wide) {
-        chunk = tile % nxw;
-        l0 = (tile / nxw) * F::NLW;
+        const int nlt = (L + F::NLW - 1) / F::NLW;
+        chunk = tile / nlt;
+        l0 = (tile - chunk * nlt) * F::NLW;
         l1 = min(L, l0 + F::NLW);
     } else {
-        const int b = tile - n_wide, nleft = ncols - nxw * F::XW;
-        chunk = nxw + b % nleft;
-        l0 = (b / nleft) * F::S;
+        const int b = tile - n_wide, nln = (L + F::S - 1) / F::S;
+        chunk = nxw + b / nln;
+        l0 = (b - (b / nln) * nln) * F::S;
         l1 = min(L, l0 + F::S);
     }
 }
@@ -190,10 +191,11 @@ template <int N> struct FusedHost {
         const int n_wide = nxw * ((L + F::NLW - 1) / F::NLW);
         out.clear();
         if (chunk < nxw) {
-            for (int lt = 0; lt < (L + F::NLW - 1) / F::NLW; ++lt) out.push_back(chunk + nxw * lt);
+            const int nlt = (L + F::NLW - 1) / F::NLW;
+            for (int lt = 0; lt < nlt; ++lt) out.push_back(chunk * nlt + lt);
         } else {
-            const int nleft = ncols - nxw * F::XW, cc = chunk - nxw;
-            for (int lt = 0; lt < (L + F::S - 1) / F::S; ++lt) out.push_back(n_wide + cc + nleft * lt);
+            const int cc = chunk - nxw, nln = (L + F::S - 1) / F::S;
+            for (int lt = 0; lt < nln; ++lt) out.push_back(n_wide + cc * nln + lt);
         }
     }
     static std::vector<int2> order() {

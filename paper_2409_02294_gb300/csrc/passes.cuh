@@ -41,6 +41,8 @@ template <class R> struct PassParams {
     int nx, ny, nz;
     long long sx;             // complex row stride of W1/W2
     unsigned* status;         // device status word (unused by these passes)
+    int tile0;                // first tile of this launch (column passes)
+    int ntile;                // tiles in this launch, 0 = all
 };
 
 // bytes of one 128-byte segment in complex elements
@@ -52,6 +54,8 @@ template <class R> struct Seg { static constexpr int XW = 128 / (int)sizeof(cpx<
 //
 // Tiles: "wide" tiles map slot -> (kx = x0 + slot % XW, other = o0 + slot /
 // XW), so XW consecutive lanes read one row segment of up to 128 bytes.
+// Tiles are numbered chunk-major (all line groups of one band of XW columns,
+// then the next band), so a range of columns is a contiguous range of tiles.
 // Columns beyond the last full segment (the Nyquist column kx = nx when nx
 // is a multiple of XW) go to "narrow" tiles: slot -> other index.
 
@@ -70,14 +74,14 @@ __device__ __forceinline__ ColTile<R, SLOTS> col_tile(int ncols, int L, int slot
     const int n_wide = nxw * wide_l;
     ColTile<R, SLOTS> c;
     int b = tile;
-    if (b < n_wide) {
-        const int xt = b % nxw, lt = b / nxw;
+    if (b < n_wide) {  // chunk-major: all line groups of band xt, then band xt + 1
+        const int xt = b / wide_l, lt = b - xt * wide_l;
         c.kx = xt * XW + slot % XW;
         c.other = lt * NLW + slot / XW;
     } else {
         b -= n_wide;
-        const int nleft = ncols - nxw * XW;
-        const int cc = b % nleft, lt = b / nleft;
+        const int narrow_l = (L + SLOTS - 1) / SLOTS;
+        const int cc = b / narrow_l, lt = b - cc * narrow_l;
         c.kx = nxw * XW + cc;
         c.other = lt * SLOTS + slot;
     }
@@ -117,6 +121,20 @@ __device__ __forceinline__ LineSmem<R> col_line(cpx<R>* sm, int half, int slot) 
     return {sm + half * col_rows<R, N, SLOTS>() * SLOTS + slot, SLOTS, ColPad<R, SLOTS>::shift,
             ColPad<R, SLOTS>::pad};
 }
+
+// Asynchronous global -> shared copy of one real value (4 or 8 bytes); it
+// has landed once cp.async.wait_group 0 returns in the issuing thread.
+template <class R> __device__ __forceinline__ void cp_async_real(R* smem, const R* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
 template <class Cfg, int SLOTS, int LPT> struct ColIds {
     int slot, t, q;
@@ -222,6 +240,22 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     cpx<R>* __restrict__ w = static_cast<cpx<R>*>(p.out);
     const long long plane = 2LL * ny * p.sx;
 
+    // start copying this column's octant row Ghat[kz][kyf][kx], kz <= N, to
+    // shared memory (after the exchange buffers); it is needed only after
+    // the forward transform
+    R* gsl = reinterpret_cast<R*>(sm + 2 * col_rows<R, N, SLOTS>() * SLOTS);
+    if (c.valid) {
+        const int kys = c.other;
+        const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
+        const int kyf = ky <= ny ? ky : 2 * ny - ky;
+        const long long gz = (long long)(ny + 1) * (nx + 1);
+        const R* g = p.greens + (long long)kyf * (nx + 1) + c.kx;
+        constexpr int TPS = (LPT == 1 ? 2 : 1) * T;  // threads per slot
+        const int u = id.t + (LPT == 1 ? id.q * T : 0);
+        for (int kz = u; kz <= N; kz += TPS) cp_async_real(gsl + id.slot * (N + 1) + kz, g + kz * gz);
+    }
+    cp_async_commit();
+
     cpx<R> v[LPT][E];
     cpx<R>* col = w + (long long)c.other * p.sx + c.kx;
 #pragma unroll
@@ -239,14 +273,13 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
     line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
-    // Green's multiply at frequency (kx, ky, kz), folded into the octant.
-    // kz = 2 (t + T m) + q is <= N exactly for m < E/2.
+    // Green's multiply at frequency (kx, ky, kz), folded into the octant;
+    // the column's octant row was copied to shared memory while the forward
+    // transform ran.  kz = 2 (t + T m) + q is <= N exactly for m < E/2.
+    cp_async_commit_wait_all();
+    __syncthreads();
     if (c.valid) {
-        const int kys = c.other;
-        const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
-        const int kyf = ky <= ny ? ky : 2 * ny - ky;
-        const long long gz = (long long)(ny + 1) * (nx + 1);
-        const R* __restrict__ g = p.greens + (long long)kyf * (nx + 1) + c.kx;
+        const R* g = gsl + id.slot * (N + 1);
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             const int kz0 = 2 * id.t + id.half(l);
@@ -254,7 +287,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
             for (int m = 0; m < E; ++m) {
                 const int kz = kz0 + 2 * T * m;
                 const int kzf = (m < E / 2) ? kz : 2 * N - kz;
-                v[l][m] = scale(v[l][m], __ldg(g + kzf * gz));
+                v[l][m] = scale(v[l][m], g[kzf]);
             }
         }
     }
@@ -547,17 +580,17 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
 template <class Cfg, int SLOTS, int LPT, int MINB>
 __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB) k_y_fwd(PassParams<typename Cfg::R> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_y_fwd<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
+    tile_y_fwd<Cfg, SLOTS, LPT, false>(p, blockIdx.x + p.tile0, smem_raw);
 }
 template <class Cfg, int SLOTS, int LPT, int MINB>
 __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB) k_z_conv(PassParams<typename Cfg::R> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_z_conv<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
+    tile_z_conv<Cfg, SLOTS, LPT, false>(p, blockIdx.x + p.tile0, smem_raw);
 }
 template <class Cfg, int SLOTS, int LPT, int MINB>
 __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB) k_y_inv(PassParams<typename Cfg::R> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_y_inv<Cfg, SLOTS, LPT, false>(p, blockIdx.x, smem_raw);
+    tile_y_inv<Cfg, SLOTS, LPT, false>(p, blockIdx.x + p.tile0, smem_raw);
 }
 template <class Cfg, int PAIRS, int LPT, int MINB>
 __global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>(), MINB) k_x_fwd(PassParams<typename Cfg::R> p, int rows) {
@@ -612,6 +645,10 @@ template <class Cfg, class V> constexpr int var_pairs() {
 template <class Cfg, int SLOTS> constexpr size_t col_smem() {
     return 2ull * col_rows<typename Cfg::R, Cfg::N, SLOTS>() * SLOTS * sizeof(cpx<typename Cfg::R>);
 }
+// the z pass also stages each column's Green's function row
+template <class Cfg, int SLOTS> constexpr size_t col_smem_z() {
+    return col_smem<Cfg, SLOTS>() + (size_t)SLOTS * (Cfg::N + 1) * sizeof(typename Cfg::R);
+}
 template <class Cfg, int PAIRS> constexpr size_t row_smem() {
     using R = typename Cfg::R;
     constexpr size_t lines = 2ull * PAIRS * row_line_stride<Cfg>() * sizeof(cpx<R>);
@@ -651,7 +688,7 @@ cudaError_t launch_col(int pass, const PassParams<typename Cfg::R>& p, cudaStrea
     constexpr int NT = col_threads<Cfg, S, L>();
     static_assert(NT <= 1024, "column CTA too large");
     const int lines = pass == 2 ? 2 * p.ny : p.nz;
-    const int grid = col_grid<R, S>(p.nx + 1, lines);
+    const int grid = p.ntile > 0 ? p.ntile : col_grid<R, S>(p.nx + 1, lines);
     if (grid == 0) return cudaSuccess;
     cudaError_t e;
     if (pass == 1) {
@@ -661,8 +698,10 @@ cudaError_t launch_col(int pass, const PassParams<typename Cfg::R>& p, cudaStrea
         if ((e = set_smem<SmemTag<3, Cfg, S, L * 16 + V::MINB>>(k_y_inv<Cfg, S, L, V::MINB>, sm)) != cudaSuccess) return e;
         k_y_inv<Cfg, S, L, V::MINB><<<grid, NT, sm, st>>>(p);
     } else {
-        if ((e = set_smem<SmemTag<2, Cfg, S, L * 16 + V::MINB>>(k_z_conv<Cfg, S, L, V::MINB>, sm)) != cudaSuccess) return e;
-        k_z_conv<Cfg, S, L, V::MINB><<<grid, NT, sm, st>>>(p);
+        constexpr size_t smz = col_smem_z<Cfg, S>();
+        if ((e = set_smem<SmemTag<2, Cfg, S, L * 16 + V::MINB>>(k_z_conv<Cfg, S, L, V::MINB>, smz)) != cudaSuccess)
+            return e;
+        k_z_conv<Cfg, S, L, V::MINB><<<grid, NT, smz, st>>>(p);
     }
     return cudaGetLastError();
 }

@@ -137,13 +137,13 @@ __device__ __forceinline__ void tile_z_conv_tc(const PassParams<float>& p, int t
 template <int N, bool BF16>
 __global__ void __launch_bounds__(256) k_z_conv_tc(PassParams<float> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_z_conv_tc<N, BF16, false>(p, blockIdx.x, smem_raw);
+    tile_z_conv_tc<N, BF16, false>(p, blockIdx.x + p.tile0, smem_raw);
 }
 
 template <int N, bool BF16>
 cudaError_t launch_z_tc_n(const PassParams<float>& p, cudaStream_t st) {
     constexpr size_t sm = 128ull * N + 4ull * 8 * (N + 1);
-    const int grid = col_grid<float, 8>(p.nx + 1, 2 * p.ny);
+    const int grid = p.ntile > 0 ? p.ntile : col_grid<float, 8>(p.nx + 1, 2 * p.ny);
     if (grid == 0) return cudaSuccess;
     cudaError_t e;
     if ((e = set_smem<SmemTag<20 + BF16, LineCfg<float, N, 16, Radices<N>>, 8, 1>>(k_z_conv_tc<N, BF16>, sm)))

@@ -29,6 +29,9 @@ struct poisson_plan_s {
     void* fused_ctl;
     int fused_total;
     int fused_ctl_words;
+    cudaStream_t band_stream[8];  // banded execution: one stream per kx band
+    cudaEvent_t band_ev_x, band_ev_y[8], band_ev_done[8];
+    bool band_ready;
 };
 
 namespace pgb {

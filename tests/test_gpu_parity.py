@@ -349,3 +349,22 @@ def test_fused_mode_rejected_for_unsupported_shapes(pg):
     with pg.Plan(64, 32, 32) as plan:
         with pytest.raises(pg.PoissonError):
             plan.set_variant(5, 1)
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (48, 96, 192), (256, 256, 256), (32, 64, 512)])
+@pytest.mark.parametrize("mode", [3, 4])
+def test_banded_execution_matches_oracle(pg, oracle_mod, shape, mode):
+    nz, ny, nx = shape
+    rho = np.random.default_rng(sum(shape) + mode).standard_normal(shape).astype(np.float32)
+    ref = oracle_mod.solve_fft(rho.astype(np.float64))
+    x = torch.from_numpy(rho).cuda()
+    with pg.Plan(nx, ny, nz) as plan:
+        counts = plan.info()["variant_count"]
+        for v in (0, 2, 4):  # band ranges follow each pass's tile width
+            for pss in range(5):
+                plan.set_variant(pss, min(v, counts[pss] - 1))
+            plan.set_variant(5, mode)
+            for _ in range(2):
+                out = plan.solve(x).double().cpu().numpy()
+                l2, mx = rel_errors(out, ref)
+                assert l2 <= TOL32[0] and mx <= TOL32[1], (v, l2, mx)
