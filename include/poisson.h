@@ -116,15 +116,31 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, voi
 /*
  * Solve `count` independent fields, plans[i] applied to rho_dev[i] ->
  * phi_dev[i].  Plans may have different sizes but must share the device
- * and precision (FP32).  The first call with a given plan list builds a
- * tile table and a CUDA graph of one persistent kernel; later calls with the
- * same list replay it.  The arrays of pointers are host arrays.  Errors:
- * POISSON_ERR_ARG, POISSON_ERR_UNSUPPORTED (mixed precision), POISSON_ERR_CUDA,
- * POISSON_ERR_TIMEOUT (reported by poisson_plan_sync_status on plans[0]).
+ * and precision (FP32).  Two executions exist, each replayed from a CUDA
+ * graph: (0) one persistent kernel over the tiles of all fields, with
+ * bounded per-field dependency waits; (1) every field's own five kernels,
+ * captured into one graph that spreads the fields over four streams.  The
+ * first call with a given plan list builds both, times them on the caller's
+ * data (synchronising cuda_stream) and keeps the faster; the environment
+ * variable POISSON_BATCH_MODE=0 or 1 forces one.  Later calls replay the
+ * chosen graph (mode 1 re-captures when the buffers change).  The arrays of
+ * pointers are host arrays.  Errors: POISSON_ERR_ARG, POISSON_ERR_UNSUPPORTED
+ * (mixed precision or devices), POISSON_ERR_CUDA, POISSON_ERR_TIMEOUT
+ * (reported by poisson_plan_sync_status on plans[0]).
  */
 poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count,
                                      const void* const* rho_dev, void* const* phi_dev,
                                      void* cuda_stream);
+
+/*
+ * Execution mode of the batch cached for this plan list (after a first
+ * poisson_solve_batched call with it): 0 persistent kernel, 1 per-field
+ * launches, -1 not decided yet.  set_mode = -1 makes the next call time both
+ * again.  Errors: POISSON_ERR_ARG (bad arguments, or set_mode on a plan list
+ * that has no cached batch yet).
+ */
+poisson_status poisson_batch_get_mode(poisson_plan_t const* plans, int count, int* mode);
+poisson_status poisson_batch_set_mode(poisson_plan_t const* plans, int count, int mode);
 
 /*
  * End-to-end solve through host buffers: copies rho_host (nx*ny*nz values)

@@ -18,10 +18,11 @@ from . import abi  # noqa: F401
 from .abi import (  # noqa: F401
     Plan,
     PoissonError,
+    batch_mode,
     PoissonSolve,
     lib,
     solve_batched,
     supported_size,
 )
 
-__all__ = ["Plan", "PoissonError", "PoissonSolve", "lib", "solve_batched", "supported_size"]
+__all__ = ["Plan", "PoissonError", "PoissonSolve", "batch_mode", "lib", "solve_batched", "supported_size"]

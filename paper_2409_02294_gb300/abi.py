@@ -52,6 +52,8 @@ SIGNATURES = [
     ("poisson_solve_adjoint", _I, [_P, _P, _P, _P]),
     ("poisson_solve_batched", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("poisson_solve_host", _I, [_P, _P, _P, _P]),
+    ("poisson_batch_get_mode", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I)]),
+    ("poisson_batch_set_mode", _I, [ctypes.POINTER(_P), _I, _I]),
     ("poisson_solve_pass", _I, [_P, _I, _P, _P, _P]),
     ("poisson_plan_destroy", _I, [_P]),
     ("poisson_plan_get_info", _I, [_P, ctypes.POINTER(PlanInfo)]),
@@ -265,6 +267,23 @@ def solve_noalloc(rho, h=1.0, G=1.0, out=None, stream=None):
                                        ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                        _stream_handle(stream)), "poisson_solve_noalloc")
     return out
+
+
+def _plan_array(plans):
+    PA = ctypes.c_void_p * max(len(plans), 1)
+    return PA(*[p.handle for p in plans])
+
+
+def batch_mode(plans, mode=None):
+    """Get (mode=None) or set the execution mode of the batch cached for
+    this plan list: 0 persistent kernel, 1 per-field launches, -1 undecided."""
+    hp = _plan_array(plans)
+    if mode is None:
+        out = ctypes.c_int(-1)
+        _check(lib().poisson_batch_get_mode(hp, len(plans), ctypes.byref(out)), "poisson_batch_get_mode")
+        return out.value
+    _check(lib().poisson_batch_set_mode(hp, len(plans), int(mode)), "poisson_batch_set_mode")
+    return int(mode)
 
 
 def _make_autograd():

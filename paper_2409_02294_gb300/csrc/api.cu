@@ -325,6 +325,12 @@ poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStr
 
 }  // namespace
 
+namespace pgb {
+cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
+    return run_pass(pl, pass, rho, phi, st);
+}
+}  // namespace pgb
+
 extern "C" {
 
 const char* poisson_status_string(poisson_status s) {
@@ -531,6 +537,16 @@ poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream) 
     if (h & 2u) return POISSON_ERR_TIMEOUT;
     if (h & 1u) return POISSON_ERR_NUMERIC;
     return POISSON_OK;
+}
+
+poisson_status poisson_batch_get_mode(poisson_plan_t const* plans, int count, int* mode) {
+    if (!plans || count <= 0 || !mode) return POISSON_ERR_ARG;
+    return pgb::batch_mode(plans, count, -2, mode);
+}
+
+poisson_status poisson_batch_set_mode(poisson_plan_t const* plans, int count, int mode) {
+    if (!plans || count <= 0 || mode < -1 || mode > 1) return POISSON_ERR_ARG;
+    return pgb::batch_mode(plans, count, mode, nullptr);
 }
 
 poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count, const void* const* rho_dev,

@@ -1,5 +1,12 @@
-// Batched solve of many independent fields of uneven sizes in ONE persistent
-// kernel launch, replayed from a CUDA graph.
+// Batched solve of many independent fields of uneven sizes, replayed from a
+// CUDA graph, in one of two executions (the first call times both on the
+// caller's data and keeps the faster; POISSON_BATCH_MODE=0/1 forces one):
+//
+//  mode 0: ONE persistent kernel over the tiles of all fields (below);
+//  mode 1: every field's own five (autotuned) kernels, captured once into a
+//          graph whose branches spread the fields over four streams
+//          (largest fields first, each to the least loaded stream), so small
+//          fields run side by side.
 //
 // Work items are tiles of the five passes of every field.  The queue is laid
 // out pass-major (all x-forward tiles, then all y-forward tiles, ...) with
@@ -187,9 +194,17 @@ int tiles_for(int N, int pass, int nx, int ny, int nz) {
     }
 }
 
+constexpr int BATCH_STREAMS = 4;
+
 struct BatchState {
     std::vector<poisson_plan_t> plans;
     int hold_field = -1;
+    int mode = -1;                   // 0 persistent kernel, 1 per-field launches, -1 undecided
+    cudaStream_t side[BATCH_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
+    cudaGraphExec_t lexec = nullptr;  // mode-1 graph, for the pointers in lrho/lphi
+    std::vector<const void*> lrho;
+    std::vector<void*> lphi;
     int device = 0;
     BatchField* h_fields = nullptr;  // pinned mirror of d_fields
     BatchField* d_fields = nullptr;
@@ -207,6 +222,12 @@ std::vector<BatchState*> g_cache;
 
 void destroy_state(BatchState* b) {
     if (!b) return;
+    if (b->lexec) cudaGraphExecDestroy(b->lexec);
+    for (int k = 0; k < BATCH_STREAMS; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->copied) cudaEventDestroy(b->copied);
@@ -325,7 +346,85 @@ bool same_plans(const BatchState* b, poisson_plan_t const* plans, int count, int
     return true;
 }
 
+// Queue every field's five kernels, spread over the side streams (forked
+// from and joined back to `st`); usable eagerly or under stream capture.
+cudaError_t enqueue_fields(BatchState* b, const void* const* rho, void* const* phi, cudaStream_t st) {
+    cudaError_t e;
+    const int n = (int)b->plans.size();
+    if (!b->fork) {
+        if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming))) return e;
+        for (int k = 0; k < BATCH_STREAMS; ++k) {
+            if ((e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking))) return e;
+            if ((e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming))) return e;
+        }
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto cells = [&](int i) {
+        const poisson_plan_s* p = b->plans[i];
+        return (double)p->nx * p->ny * p->nz;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cells(x) > cells(y); });
+    double load[BATCH_STREAMS] = {0, 0, 0, 0};
+    if ((e = cudaEventRecord(b->fork, st))) return e;
+    for (int k = 0; k < BATCH_STREAMS; ++k)
+        if ((e = cudaStreamWaitEvent(b->side[k], b->fork, 0))) return e;
+    for (int i : order) {
+        int k = 0;
+        for (int j = 1; j < BATCH_STREAMS; ++j)
+            if (load[j] < load[k]) k = j;
+        load[k] += cells(i);
+        for (int pass = 0; pass < 5; ++pass)
+            if ((e = plan_run_pass(b->plans[i], pass, rho[i], phi[i], b->side[k]))) return e;
+    }
+    for (int k = 0; k < BATCH_STREAMS; ++k) {
+        if ((e = cudaEventRecord(b->join[k], b->side[k]))) return e;
+        if ((e = cudaStreamWaitEvent(st, b->join[k], 0))) return e;
+    }
+    return cudaSuccess;
+}
+
+// (Re)build the mode-1 graph for these buffers.
+cudaError_t build_launch_graph(BatchState* b, const void* const* rho, void* const* phi) {
+    cudaError_t e;
+    if (b->lexec) {
+        cudaGraphExecDestroy(b->lexec);
+        b->lexec = nullptr;
+    }
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) return e;
+    // warm the kernels (attributes, module loading) outside the capture
+    e = enqueue_fields(b, rho, phi, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue_fields(b, rho, phi, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->lexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    const int n = (int)b->plans.size();
+    b->lrho.assign(rho, rho + n);
+    b->lphi.assign(phi, phi + n);
+    return e;
+}
+
 }  // namespace
+
+poisson_status batch_mode(poisson_plan_t const* plans, int count, int set_to, int* get) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (BatchState* c : g_cache) {
+        if (!same_plans(c, plans, count, -1)) continue;
+        if (get) *get = c->mode;
+        if (set_to >= -1) c->mode = set_to;
+        return POISSON_OK;
+    }
+    if (get) *get = -1;
+    return set_to >= -1 ? POISSON_ERR_ARG : POISSON_OK;
+}
 
 void batch_forget_plan(poisson_plan_t plan) {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -382,8 +481,43 @@ poisson_status batched_solve(poisson_plan_t const* plans, int count, const void*
         if ((e = cudaEventRecord(b->copied, st))) return POISSON_ERR_CUDA;
         b->have_ptrs = true;
     }
-    if ((e = cudaGraphLaunch(b->exec, st))) return POISSON_ERR_CUDA;
-    return POISSON_OK;
+    // mode 1 needs a graph captured for exactly these buffers
+    auto launch_mode1 = [&]() -> cudaError_t {
+        bool same = b->lexec != nullptr;
+        for (int i = 0; i < count && same; ++i) same = b->lrho[i] == rho[i] && b->lphi[i] == phi[i];
+        if (!same && (e = build_launch_graph(b, rho, phi))) return e;
+        return cudaGraphLaunch(b->lexec, st);
+    };
+    if (b->mode < 0) {
+        const char* forced = std::getenv("POISSON_BATCH_MODE");
+        if (hold >= 0) {
+            b->mode = 0;
+        } else if (forced && (forced[0] == '0' || forced[0] == '1')) {
+            b->mode = forced[0] - '0';
+        } else {
+            // time both executions on the caller's data (twice each, keep the
+            // second) and keep the faster
+            cudaEvent_t t0, t1;
+            if ((e = cudaEventCreate(&t0)) || (e = cudaEventCreate(&t1))) return POISSON_ERR_CUDA;
+            float ms[2] = {0.f, 0.f};
+            for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+                for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                    if ((e = cudaEventRecord(t0, st))) break;
+                    e = m == 0 ? cudaGraphLaunch(b->exec, st) : launch_mode1();
+                    if (e) break;
+                    if ((e = cudaEventRecord(t1, st))) break;
+                    if ((e = cudaEventSynchronize(t1))) break;
+                    e = cudaEventElapsedTime(&ms[m], t0, t1);
+                }
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            if (e != cudaSuccess) return POISSON_ERR_CUDA;
+            b->mode = ms[1] < ms[0] ? 1 : 0;
+            return POISSON_OK;  // the timing runs already produced the result
+        }
+    }
+    e = b->mode == 0 ? cudaGraphLaunch(b->exec, st) : launch_mode1();
+    return e == cudaSuccess ? POISSON_OK : POISSON_ERR_CUDA;
 }
 
 }  // namespace pgb

@@ -38,11 +38,16 @@ namespace pgb {
 // Drop every cached batched-solve graph that refers to `plan` (called when
 // the plan is destroyed).
 void batch_forget_plan(poisson_plan_t plan);
+// One pass (0..4) of the five-launch solve with the plan's kernel variants.
+cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st);
 // Single-field fused dataflow solve (fused.cu).
 template <class R> struct PassParams;
 bool fused_supported(const poisson_plan_s* pl);
 cudaError_t fused_prepare(poisson_plan_s* pl, cudaStream_t st);
 cudaError_t fused_solve(const poisson_plan_s* pl, const PassParams<float> (&p)[5], cudaStream_t st);
+// Get (get != NULL) and/or set (set_to >= -1) the execution mode of the
+// cached batch for this plan list; set_to = -2 leaves it unchanged.
+poisson_status batch_mode(poisson_plan_t const* plans, int count, int set_to, int* get);
 // The batched solve (poisson_solve_batched after argument checks).
 poisson_status batched_solve(poisson_plan_t const* plans, int count, const void* const* rho,
                              void* const* phi, cudaStream_t st);

@@ -30,16 +30,23 @@ def _rel(a, b):
     return (np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max())
 
 
-def test_batched_matches_single_solves_and_oracle(pg, oracle_mod):
+@pytest.mark.parametrize("mode", ["0", "1", "auto"])
+def test_batched_matches_single_solves_and_oracle(pg, oracle_mod, mode, monkeypatch):
+    if mode == "auto":
+        monkeypatch.delenv("POISSON_BATCH_MODE", raising=False)
+    else:
+        monkeypatch.setenv("POISSON_BATCH_MODE", mode)
     plans = [pg.Plan(s[2], s[1], s[0], h=(1.0, 0.8, 1.2)) for s in SHAPES]
     try:
-        for rep in range(2):  # first call builds the graph, second replays it
+        for rep in range(3):  # first call builds the graphs, later ones replay
             rhos = [torch.from_numpy(workloads.gaussian_blobs(s, count=6, seed=10 * rep + i)[0]
                                      .astype(np.float32)).cuda() for i, s in enumerate(SHAPES)]
             phis = [torch.empty_like(r) for r in rhos]
             pg.solve_batched(plans, rhos, phis)
             torch.cuda.synchronize()
             assert plans[0].sync_status() == 0
+            chosen = pg.batch_mode(plans)
+            assert chosen in (0, 1) and (mode == "auto" or chosen == int(mode))
             for i, (p, r, o) in enumerate(zip(plans, rhos, phis)):
                 ref = p.solve(r)
                 l2, mx = _rel(o, ref)
@@ -48,6 +55,36 @@ def test_batched_matches_single_solves_and_oracle(pg, oracle_mod):
                 ref = oracle_mod.solve_fft(rhos[i].double().cpu().numpy(), h=(1.0, 0.8, 1.2))
                 l2, mx = _rel(phis[i].double().cpu().numpy(), ref)
                 assert l2 <= 1e-6 and mx <= 1e-5
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batch_mode_switch_keeps_results(pg, monkeypatch):
+    monkeypatch.delenv("POISSON_BATCH_MODE", raising=False)
+    shapes = SHAPES[:4]
+    plans = [pg.Plan(s[2], s[1], s[0]) for s in shapes]
+    try:
+        with pytest.raises(pg.PoissonError):
+            pg.batch_mode(plans, 0)  # no cached batch for this plan list yet
+        assert pg.batch_mode(plans) == -1
+        rhos = [torch.randn(s, device="cuda") for s in shapes]
+        outs = []
+        for m in (0, 1):
+            phis = [torch.empty_like(r) for r in rhos]
+            if m == 1:
+                pg.batch_mode(plans, 1)
+            pg.solve_batched(plans, rhos, phis)
+            torch.cuda.synchronize()
+            assert plans[0].sync_status() == 0
+            if m == 0:
+                pg.batch_mode(plans, 0)
+                pg.solve_batched(plans, rhos, phis)
+                torch.cuda.synchronize()
+            assert pg.batch_mode(plans) == m
+            outs.append(phis)
+        for a, b in zip(*outs):
+            assert _rel(a, b)[0] <= 1e-6
     finally:
         for p in plans:
             p.close()
