@@ -60,6 +60,8 @@ void host_twiddle(long long j, long long n, double* c, double* s) {
 
 template <class R>
 cudaError_t upload_twiddles(int n, void** dst, cudaStream_t st) {
+    // W_2n^j, j < 2n, then the per-stage tables gathered from it on the device
+    const int entries = axis_tw_list<R>(n).total;
     std::vector<R> h(4 * (size_t)n);
     for (long long j = 0; j < 2 * n; ++j) {
         double c, s;
@@ -67,9 +69,11 @@ cudaError_t upload_twiddles(int n, void** dst, cudaStream_t st) {
         h[2 * j] = (R)c;
         h[2 * j + 1] = (R)s;
     }
-    cudaError_t e = cudaMalloc(dst, h.size() * sizeof(R));
+    cudaError_t e = cudaMalloc(dst, (size_t)entries * 2 * sizeof(R));
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(*dst, h.data(), h.size() * sizeof(R), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = fill_stage_twiddles<R>(static_cast<cpx<R>*>(*dst), n, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);  // h goes out of scope
 }

@@ -42,6 +42,28 @@ inline bool size_supported(int n) {
     }
 }
 
+// Twiddle-table layout of an axis of edge n for the precision's radix
+// sequence (every kernel that transforms lines of n uses SizeCfg<R, n>).
+template <class R> inline StageTwList axis_tw_list(int n) {
+    switch (n) {
+        case 16: return stage_tw_list<16>(typename SizeCfg<R, 16>::C::Rads{});
+        case 32: return stage_tw_list<32>(typename SizeCfg<R, 32>::C::Rads{});
+        case 48: return stage_tw_list<48>(typename SizeCfg<R, 48>::C::Rads{});
+        case 64: return stage_tw_list<64>(typename SizeCfg<R, 64>::C::Rads{});
+        case 96: return stage_tw_list<96>(typename SizeCfg<R, 96>::C::Rads{});
+        case 128: return stage_tw_list<128>(typename SizeCfg<R, 128>::C::Rads{});
+        case 192: return stage_tw_list<192>(typename SizeCfg<R, 192>::C::Rads{});
+        case 256: return stage_tw_list<256>(typename SizeCfg<R, 256>::C::Rads{});
+        case 384: return stage_tw_list<384>(typename SizeCfg<R, 384>::C::Rads{});
+        case 512: return stage_tw_list<512>(typename SizeCfg<R, 512>::C::Rads{});
+        default: return StageTwList{};
+    }
+}
+
+// Fill the stage tables of an axis table whose first 2n entries (W_2n^j)
+// are already on the device (async on st).
+template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, cudaStream_t st);
+
 // Variants the autotuner chooses from (per pass and edge length).
 //   column passes (y forward, z convolve, y inverse): lines per thread and
 //   CTA threads; row passes (x forward, x inverse) likewise.

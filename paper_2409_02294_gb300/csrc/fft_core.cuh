@@ -11,7 +11,8 @@
 // Butterflies use twiddle constants folded at compile time (cos(2*pi*u/96)
 // table below, values from the exact trigonometric definition); the
 // inter-stage twiddles come from a per-axis table of the 2N-th roots of
-// unity computed in FP64 on the host and rounded once.
+// unity computed in FP64 on the host and rounded once, re-laid out per stage
+// (below) so that a warp's twiddle reads are contiguous.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,6 +58,18 @@ template <class R> __device__ __forceinline__ cpx<R> ldg_c(const cpx<R>* p) {
     } else {
         double2 v = __ldg(reinterpret_cast<const double2*>(p));
         return {v.x, v.y};
+    }
+}
+
+// two adjacent entries p[0], p[1] (p 16-byte aligned)
+template <class R> __device__ __forceinline__ void ldg_c2(const cpx<R>* p, cpx<R>& a, cpx<R>& b) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        a = {v.x, v.y};
+        b = {v.z, v.w};
+    } else {
+        a = ldg_c(p);
+        b = ldg_c(p + 1);
     }
 }
 
@@ -245,6 +258,53 @@ template <int... Rs> struct Radices {};
 template <int A, int... Rs> struct RadProd { static constexpr int v = A * RadProd<Rs...>::v; };
 template <int A> struct RadProd<A> { static constexpr int v = A; };
 
+// --------------------------------------------------------------------------
+// per-stage twiddle tables
+// --------------------------------------------------------------------------
+// A Stockham stage with NS > 1 multiplies input r of butterfly k (k < NS) by
+// W_{NS RAD}^{r k}.  Read straight from the W_2N table, lanes with
+// consecutive k are r*k entries apart and one warp request touches up to 16
+// cache lines.  So every such stage gets its own table, stored after the 2N
+// entries of W_2N^j, with k fastest:
+//   RAD == 2: entry k                      = W_{2 NS}^k
+//   RAD >  2: entry 2 (p NS + k) + i       = W_{NS RAD}^{(2p+1+i) k},  p < RAD/2, i < 2
+// (pairs, so that an FP32 thread fetches two twiddles with one 16-byte load).
+// Entries are copies of W_2N entries (W_{NS RAD}^{rk} = W_2N^{rk 2N/(NS RAD)}),
+// so the transform's arithmetic is unchanged.  All radices are even, hence so
+// is every table offset and the 16-byte loads stay aligned.
+template <int NS, int RAD> constexpr int stage_tw_size() { return NS > 1 ? (RAD == 2 ? NS : NS * RAD) : 0; }
+template <int NS, int RAD, int... REST> constexpr int stage_tw_total() {
+    if constexpr (sizeof...(REST) == 0) return stage_tw_size<NS, RAD>();
+    else return stage_tw_size<NS, RAD>() + stage_tw_total<NS * RAD, REST...>();
+}
+// complex entries of an axis' twiddle table for a radix sequence
+template <int N, int... Rs> constexpr int tw_entries(Radices<Rs...>) { return 2 * N + stage_tw_total<1, Rs...>(); }
+
+// Host-side description of the stage tables of one radix sequence.
+struct StageTwList {
+    int count = 0;      // stages with a table
+    int ns[8] = {};     // their NS
+    int rad[8] = {};    // their radix
+    int off[8] = {};    // offset of their table (complex entries)
+    int total = 0;      // entries of the whole axis table
+};
+template <int N, int... Rs> StageTwList stage_tw_list(Radices<Rs...>) {
+    StageTwList L;
+    int ns = 1, off = 2 * N;
+    for (int r : {Rs...}) {
+        if (ns > 1) {
+            L.ns[L.count] = ns;
+            L.rad[L.count] = r;
+            L.off[L.count] = off;
+            off += r == 2 ? ns : ns * r;
+            ++L.count;
+        }
+        ns *= r;
+    }
+    L.total = off;
+    return L;
+}
+
 // Shared-memory view of one line's exchange buffer: element i lives at
 // base[idx(i)], idx(i) = i * stride + (i >> pad_shift) * pad.  Column tiles
 // use stride = line slots, pad = 0; row tiles use stride = 1 and one
@@ -262,32 +322,48 @@ template <class R> struct LineSmem {
 // One line per "lane set": NL independent lines (e.g. the even and odd
 // halves of a padded transform) are transformed together, stage by stage,
 // to give the scheduler independent work.  v[l][m] = x_l[t + T*m].
-// tw2N: table of W_{2N}^j, j = 0..2N-1.
-template <class R, int N, int E, bool INV, int NL, int NS, int RAD, int... REST>
+// tw2N: an axis twiddle table (W_{2N}^j, j < 2N, then the stage tables);
+// TOFF: offset of this stage's table.
+template <class R, int N, int E, bool INV, int NL, int NS, int TOFF, int RAD, int... REST>
 __device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSmem<R> (&sm)[NL],
                                          const cpx<R>* __restrict__ tw2N) {
     constexpr int T = N / E;
     constexpr int B = E / RAD;
     static_assert(E % RAD == 0, "radix must divide the per-thread element count");
+    static_assert(RAD % 2 == 0 || NS == 1, "twiddled stages need an even radix");
     constexpr bool LAST = sizeof...(REST) == 0;
     static_assert(!LAST || NS * RAD == N, "radices must multiply to N");
 #pragma unroll
     for (int g = 0; g < B; ++g) {
         const int b = t + T * g;  // butterfly index in [0, N/RAD)
         int k = 0;
-        if constexpr (NS > 1) k = b % NS;
+        if constexpr (NS > 1) {
+            k = b % NS;
+            const cpx<R>* st = tw2N + TOFF;
+            if constexpr (RAD == 2) {
+                const cpx<R> w = ldg_c(st + k);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) v[l][g + B] = cmul_dir<INV>(v[l][g + B], w);
+            } else {
+#pragma unroll
+                for (int q = 0; q < RAD / 2; ++q) {
+                    const int r0 = 2 * q + 1;
+                    cpx<R> w0, w1;
+                    if (r0 + 1 < RAD) ldg_c2(st + 2 * (q * NS + k), w0, w1);
+                    else w0 = ldg_c(st + 2 * (q * NS + k));
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) {
+                        v[l][g + B * r0] = cmul_dir<INV>(v[l][g + B * r0], w0);
+                        if (r0 + 1 < RAD) v[l][g + B * (r0 + 1)] = cmul_dir<INV>(v[l][g + B * (r0 + 1)], w1);
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             cpx<R> u[RAD];
 #pragma unroll
             for (int r = 0; r < RAD; ++r) u[r] = v[l][g + B * r];
-            if constexpr (NS > 1) {
-#pragma unroll
-                for (int r = 1; r < RAD; ++r) {
-                    const cpx<R> w = ldg_c(tw2N + r * k * (2 * N / (NS * RAD)));
-                    u[r] = cmul_dir<INV>(u[r], w);
-                }
-            }
             Dft<RAD, INV, R>::run(u);
             if constexpr (LAST) {
 #pragma unroll
@@ -306,7 +382,7 @@ __device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSm
 #pragma unroll
             for (int m = 0; m < E; ++m) v[l][m] = sm[l][t + T * m];
         __syncthreads();
-        stockham<R, N, E, INV, NL, NS * RAD, REST...>(v, t, sm, tw2N);
+        stockham<R, N, E, INV, NL, NS * RAD, TOFF + stage_tw_size<NS, RAD>(), REST...>(v, t, sm, tw2N);
     }
 }
 
@@ -314,7 +390,7 @@ template <class R, int N, int E, bool INV, int NL, int... Rs>
 __device__ __forceinline__ void line_fft(cpx<R> (&v)[NL][E], int t, const LineSmem<R> (&sm)[NL],
                                          const cpx<R>* __restrict__ tw2N, Radices<Rs...>) {
     static_assert(RadProd<Rs...>::v == N, "radices must multiply to N");
-    stockham<R, N, E, INV, NL, 1, Rs...>(v, t, sm, tw2N);
+    stockham<R, N, E, INV, NL, 1, 2 * N, Rs...>(v, t, sm, tw2N);
 }
 
 }  // namespace pgb
