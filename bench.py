@@ -427,7 +427,14 @@ def run_ours(args):
     rhos = [torch.from_numpy(r).to(dev) for r in rhos32]
     phis = [torch.empty_like(r) for r in rhos]
     rho, phi = rhos[0], phis[0]
-    plan = pg.Plan(n, n, n, precision=args.precision, flags=pg.abi.FLAG_AUTOTUNE)
+    if args.variants:
+        # fixed kernel variants (x fwd, y fwd, z, y inv, x inv, execution mode),
+        # no autotuning: for profiling one known configuration
+        plan = pg.Plan(n, n, n, precision=args.precision)
+        for i, v in enumerate(int(x) for x in args.variants.split(",")):
+            plan.set_variant(i, v)
+    else:
+        plan = pg.Plan(n, n, n, precision=args.precision, flags=pg.abi.FLAG_AUTOTUNE)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -617,6 +624,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--variants", default="",
+                    help="comma list of kernel variants per pass (and execution mode): skip autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -228,6 +228,31 @@ __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cf
 // pass 2: pad + FFT along z, multiply by Ghat, inverse FFT along z, crop.
 // In place on W2.  Ghat is real (the kernel is real and even), so the
 // adjoint's conj(Ghat) is the same multiply.
+// Staging of a tile's Green's function rows in shared memory: row kz
+// (kz <= N) holds the SLOTS columns' values.  With SLOTS < BW (elements per
+// row of banks) a row covers one of G = BW/SLOTS bank windows; rows are
+// permuted within aligned blocks of G so that row kz = 2a + b sits in window
+// (a + b G/2) mod G.  The copy-in (lanes on G consecutive rows of a block)
+// and the multiply (lanes on G rows two apart, either direction) then never
+// put two lanes of a warp on one bank.
+template <class R, int SLOTS> constexpr int gsl_group() {
+    constexpr int BW = 128 / (int)sizeof(R);
+    return SLOTS >= BW ? 1 : BW / SLOTS;
+}
+template <class R, int SLOTS> __device__ __forceinline__ int gsl_idx(int kz, int slot) {
+    constexpr int G = gsl_group<R, SLOTS>();
+    if constexpr (G == 1) {
+        return kz * SLOTS + slot;
+    } else {
+        const int w = ((kz >> 1) + (kz & 1) * (G / 2)) & (G - 1);
+        return ((kz & ~(G - 1)) + w) * SLOTS + slot;
+    }
+}
+template <class R, int N, int SLOTS> constexpr int gsl_elems() {
+    constexpr int G = gsl_group<R, SLOTS>();
+    return (N + 1 + G - 1) / G * G * SLOTS;
+}
+
 template <class Cfg, int SLOTS, int LPT, bool CG>
 __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p, int tile,
                                             unsigned char* smem_raw) {
@@ -252,7 +277,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
         const R* g = p.greens + (long long)kyf * (nx + 1) + c.kx;
         constexpr int TPS = (LPT == 1 ? 2 : 1) * T;  // threads per slot
         const int u = id.t + (LPT == 1 ? id.q * T : 0);
-        for (int kz = u; kz <= N; kz += TPS) cp_async_real(gsl + id.slot * (N + 1) + kz, g + kz * gz);
+        for (int kz = u; kz <= N; kz += TPS) cp_async_real(gsl + gsl_idx<R, SLOTS>(kz, id.slot), g + kz * gz);
     }
     cp_async_commit();
 
@@ -279,7 +304,6 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     cp_async_commit_wait_all();
     __syncthreads();
     if (c.valid) {
-        const R* g = gsl + id.slot * (N + 1);
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             const int kz0 = 2 * id.t + id.half(l);
@@ -287,7 +311,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
             for (int m = 0; m < E; ++m) {
                 const int kz = kz0 + 2 * T * m;
                 const int kzf = (m < E / 2) ? kz : 2 * N - kz;
-                v[l][m] = scale(v[l][m], g[kzf]);
+                v[l][m] = scale(v[l][m], gsl[gsl_idx<R, SLOTS>(kzf, id.slot)]);
             }
         }
     }
@@ -647,7 +671,7 @@ template <class Cfg, int SLOTS> constexpr size_t col_smem() {
 }
 // the z pass also stages each column's Green's function row
 template <class Cfg, int SLOTS> constexpr size_t col_smem_z() {
-    return col_smem<Cfg, SLOTS>() + (size_t)SLOTS * (Cfg::N + 1) * sizeof(typename Cfg::R);
+    return col_smem<Cfg, SLOTS>() + (size_t)gsl_elems<typename Cfg::R, Cfg::N, SLOTS>() * sizeof(typename Cfg::R);
 }
 template <class Cfg, int PAIRS> constexpr size_t row_smem() {
     using R = typename Cfg::R;
