@@ -133,6 +133,14 @@ poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count,
                                      void* cuda_stream);
 
 /*
+ * Kernel launches one poisson_solve of this plan makes in its current
+ * configuration (variants and execution mode), counted by capturing a solve
+ * into a CUDA graph on a private stream (nothing is executed).  Memset and
+ * event nodes are not counted.  Errors: POISSON_ERR_ARG, POISSON_ERR_CUDA.
+ */
+poisson_status poisson_plan_launch_count(poisson_plan_t plan, int* launches);
+
+/*
  * Execution mode of the batch cached for this plan list (after a first
  * poisson_solve_batched call with it): 0 persistent kernel, 1 per-field
  * launches, -1 not decided yet.  set_mode = -1 makes the next call time both

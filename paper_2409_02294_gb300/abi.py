@@ -52,6 +52,7 @@ SIGNATURES = [
     ("poisson_solve_adjoint", _I, [_P, _P, _P, _P]),
     ("poisson_solve_batched", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("poisson_solve_host", _I, [_P, _P, _P, _P]),
+    ("poisson_plan_launch_count", _I, [_P, ctypes.POINTER(_I)]),
     ("poisson_batch_get_mode", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I)]),
     ("poisson_batch_set_mode", _I, [ctypes.POINTER(_P), _I, _I]),
     ("poisson_solve_pass", _I, [_P, _I, _P, _P, _P]),
@@ -152,6 +153,12 @@ class Plan:
         out["variant"] = list(inf.variant)
         out["variant_count"] = list(inf.variant_count)
         return out
+
+    def launch_count(self):
+        """Kernel launches one solve makes in the current configuration."""
+        n = ctypes.c_int(0)
+        _check(lib().poisson_plan_launch_count(self.handle, ctypes.byref(n)), "poisson_plan_launch_count")
+        return n.value
 
     def autotune(self, stream=None):
         _check(lib().poisson_plan_autotune(self.handle, _stream_handle(stream)), "poisson_plan_autotune")

@@ -156,10 +156,10 @@ poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStr
 bool banded_supported(const poisson_plan_s* pl);
 
 // Default variant per pass before (or without) autotuning: the ones the
-// autotuner picks for 256^3 and 512^3 grids on GB300.
+// autotuner picks for the 256^3 FP32 grid on GB300.
 int default_variant(poisson_precision prec, int pass) {
     if (prec == POISSON_FP64) return 0;
-    static const int fp32_default[5] = {1, 0, 0, 2, 1};
+    static const int fp32_default[5] = {3, 5, 5, 1, 3};
     return fp32_default[pass];
 }
 
@@ -541,6 +541,41 @@ poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream) 
     if (h & 2u) return POISSON_ERR_TIMEOUT;
     if (h & 1u) return POISSON_ERR_NUMERIC;
     return POISSON_OK;
+}
+
+poisson_status poisson_plan_launch_count(poisson_plan_t plan, int* launches) {
+    if (!plan || !launches) return POISSON_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) {
+        if (cudaSetDevice(plan->device) != cudaSuccess) return POISSON_ERR_CUDA;
+    }
+    if (plan->use_fused >= 3 && band_prepare(plan) != cudaSuccess) return POISSON_ERR_CUDA;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return POISSON_ERR_CUDA;
+    // capture one solve (nothing runs; the plan's work buffer stands in for rho and phi)
+    poisson_status rs = POISSON_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        rs = solve_all(plan, plan->w1, plan->w1, s);
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess) rs = POISSON_ERR_CUDA;
+    }
+    int n = 0;
+    if (rs == POISSON_OK && g) {
+        size_t count = 0;
+        if (cudaGraphGetNodes(g, nullptr, &count) != cudaSuccess) rs = POISSON_ERR_CUDA;
+        std::vector<cudaGraphNode_t> nodes(count);
+        if (rs == POISSON_OK && count && cudaGraphGetNodes(g, nodes.data(), &count) != cudaSuccess)
+            rs = POISSON_ERR_CUDA;
+        for (size_t i = 0; rs == POISSON_OK && i < count; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) rs = POISSON_ERR_CUDA;
+            else if (t == cudaGraphNodeTypeKernel) ++n;
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(s);
+    if (rs == POISSON_OK) *launches = n;
+    return rs;
 }
 
 poisson_status poisson_batch_get_mode(poisson_plan_t const* plans, int count, int* mode) {

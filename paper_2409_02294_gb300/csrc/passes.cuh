@@ -21,6 +21,7 @@
 #pragma once
 
 #include "fft_core.cuh"
+#include "tma.cuh"
 
 namespace pgb {
 
@@ -152,10 +153,33 @@ template <class Cfg, int SLOTS, int LPT> constexpr int col_threads() {
     return (LPT == 1 ? 2 : 1) * SLOTS * Cfg::T;
 }
 
+// Where a column tile's input comes from: straight from global memory
+// (ColFromGlobal) or from a copy of the tile in shared memory that a TMA load
+// placed there (ColFromSmem: element of tile row r at base[r * stride]).
+// The hook runs right after the inputs are in registers; the TMA kernel
+// uses it to start loading its next tile into the same buffer.
+struct ColFromGlobal {};
+template <class R> struct ColFromSmem {
+    const cpx<R>* base;
+    int stride;
+};
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+template <bool CG, class R>
+__device__ __forceinline__ cpx<R> col_in(const ColFromGlobal&, const cpx<R>* g, int) {
+    return ld_c<CG>(g);
+}
+template <bool CG, class R>
+__device__ __forceinline__ cpx<R> col_in(const ColFromSmem<R>& s, const cpx<R>*, int row) {
+    return s.base[row * s.stride];
+}
+
 // pass 1: pad + forward FFT along y.  W1 -> W2.
-template <class Cfg, int SLOTS, int LPT, bool CG>
+template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p, int tile,
-                                            unsigned char* smem_raw) {
+                                            unsigned char* smem_raw, const In& in_src = In{},
+                                            const Hook& after_load = Hook{}) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -169,7 +193,9 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
     cpx<R> v[LPT][E];
     const cpx<R>* src = in + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[0][m] = c.valid ? ld_c<CG>(src + (long long)(T * m) * sx) : cpx<R>{0, 0};
+    for (int m = 0; m < E; ++m)
+        v[0][m] = c.valid ? col_in<CG>(in_src, src + (long long)(T * m) * sx, id.t + T * m) : cpx<R>{0, 0};
+    after_load();
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
@@ -253,9 +279,10 @@ template <class R, int N, int SLOTS> constexpr int gsl_elems() {
     return (N + 1 + G - 1) / G * G * SLOTS;
 }
 
-template <class Cfg, int SLOTS, int LPT, bool CG>
+template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p, int tile,
-                                            unsigned char* smem_raw) {
+                                            unsigned char* smem_raw, const In& in_src = In{},
+                                            const Hook& after_load = Hook{}) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -285,7 +312,8 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     cpx<R>* col = w + (long long)c.other * p.sx + c.kx;
 #pragma unroll
     for (int m = 0; m < E; ++m)
-        v[0][m] = c.valid ? ld_c<CG>(col + (long long)(id.t + T * m) * plane) : cpx<R>{0, 0};
+        v[0][m] = c.valid ? col_in<CG>(in_src, col + (long long)(id.t + T * m) * plane, id.t + T * m) : cpx<R>{0, 0};
+    after_load();
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
@@ -325,9 +353,10 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
 }
 
 // pass 3: inverse FFT along y + crop.  W2 -> W1.
-template <class Cfg, int SLOTS, int LPT, bool CG>
+template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p, int tile,
-                                            unsigned char* smem_raw) {
+                                            unsigned char* smem_raw, const In& in_src = In{},
+                                            const Hook& after_load = Hook{}) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -344,8 +373,11 @@ __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p,
         const cpx<R>* src = in + (long long)c.other * 2 * ny * sx + c.kx +
                             (long long)(id.half(l) * ny + id.t) * sx;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[l][m] = c.valid ? ld_c<CG>(src + (long long)(T * m) * sx) : cpx<R>{0, 0};
+        for (int m = 0; m < E; ++m)
+            v[l][m] = c.valid ? col_in<CG>(in_src, src + (long long)(T * m) * sx, id.half(l) * ny + id.t + T * m)
+                              : cpx<R>{0, 0};
     }
+    after_load();
     LineSmem<R> ls[LPT];
 #pragma unroll
     for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
@@ -627,6 +659,96 @@ __global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>(), MINB) k_x_inv(
     tile_x_inv<Cfg, PAIRS, LPT, false>(p, rows, blockIdx.x, smem_raw);
 }
 
+// --------------------------------------------------------------------------
+// Persistent column kernels with TMA prefetch (FP32, wide tiles)
+// --------------------------------------------------------------------------
+//
+// Each CTA walks tiles t0 + blockIdx.x, + gridDim.x, ... of [t0, t1).  A
+// tile's input (ROWS rows x SLOTS columns) is one 3-D box of the W1/W2 array
+// (up to 256 rows per TMA copy), copied into one of two shared-memory
+// buffers; once every thread holds tile i in registers, thread 0 starts the
+// copy of tile i+2 into the buffer tile i came from, so two tiles' loads are
+// always in flight under the transforms.  Box layouts in shared memory:
+//   y passes (PASS 1, 3): [other][row][kx]   (other = z, outermost dim)
+//   z pass (PASS 2):      [row][other][kx]   (other = ky line, middle dim)
+template <int PASS, class Cfg, int SLOTS> struct TmaBox {
+    static constexpr int ROWS = PASS == 3 ? 2 * Cfg::N : Cfg::N;
+    static constexpr int XW = SLOTS < Seg<float>::XW ? SLOTS : Seg<float>::XW;
+    static constexpr int NLW = SLOTS / XW;
+    // rows per copy: the largest of ROWS, 256, 192, 128 that divides ROWS and is <= 256 (box limit)
+    static constexpr int CH = ROWS <= 256 ? ROWS : ROWS % 256 == 0 ? 256 : ROWS % 192 == 0 ? 192 : 128;
+    static constexpr int NCH = ROWS / CH;
+    static constexpr unsigned BYTES = (unsigned)ROWS * SLOTS * 8u;  // one buffer
+    static constexpr size_t WORK_OFF = 2ull * BYTES + 128;          // two mbarriers, then the work area
+    static_assert(ROWS % CH == 0, "rows must split into whole copies");
+    static_assert(NCH == 1 || NLW == 1, "more than 256 rows needs one line per box column");
+};
+constexpr int kTmaWaitPolls = 1 << 20;  // bounded wait for one tile's copy
+
+template <int PASS, class Cfg, int SLOTS, int LPT, int MINB>
+__global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
+    k_col_tma(PassParams<float> p, const __grid_constant__ CUtensorMap map, int t0, int t1) {
+    using B = TmaBox<PASS, Cfg, SLOTS>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<float>* buf = reinterpret_cast<cpx<float>*>(smem_raw);  // buffer k at buf + k * ROWS * SLOTS
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * B::BYTES);  // bar[0], bar[1]
+    unsigned char* work = smem_raw + B::WORK_OFF;
+    const int lines = PASS == 2 ? 2 * p.ny : p.nz;
+    const int wide_l = (lines + B::NLW - 1) / B::NLW;
+    auto issue = [&](int tile, int k) {
+        const int xt = tile / wide_l, lt = tile - xt * wide_l;
+        const int c0 = 2 * xt * B::XW, o0 = lt * B::NLW;
+        cpx<float>* dst = buf + k * B::ROWS * SLOTS;
+        mbar_arrive_expect_tx(bar + k, B::BYTES);
+#pragma unroll
+        for (int ch = 0; ch < B::NCH; ++ch) {
+            if constexpr (PASS == 2) tma_load_3d(dst + ch * B::CH * SLOTS, &map, bar + k, c0, o0, ch * B::CH);
+            else tma_load_3d(dst + ch * B::CH * B::XW, &map, bar + k, c0, ch * B::CH, o0);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int tile = t0 + (int)blockIdx.x;
+    if (tile >= t1) return;
+    const int G = (int)gridDim.x;
+    if (threadIdx.x == 0) {
+        issue(tile, 0);
+        if (tile + G < t1) issue(tile + G, 1);
+    }
+    const int slot = threadIdx.x % SLOTS;
+    const int off = PASS == 2 ? slot : (slot / B::XW) * B::ROWS * B::XW + slot % B::XW;
+    const int stride = PASS == 2 ? SLOTS : B::XW;
+    unsigned parity = 0;  // bit k: phase parity of bar[k]
+    for (int k = 0; tile < t1; tile += G, k ^= 1) {
+        const bool ok = __syncthreads_and(mbar_wait(bar + k, (parity >> k) & 1u, kTmaWaitPolls));
+        if (!ok) {
+            // record the timeout, give the copies in flight a last bounded
+            // chance to land, and leave (uniformly for the whole CTA)
+            if (threadIdx.x == 0 && p.status) atomicOr(p.status, 2u);
+            (void)mbar_wait(bar + k, (parity >> k) & 1u, kTmaWaitPolls);
+            if (tile + G < t1) (void)mbar_wait(bar + (k ^ 1), (parity >> (k ^ 1)) & 1u, kTmaWaitPolls);
+            return;
+        }
+        parity ^= 1u << k;
+        const ColFromSmem<float> in{buf + k * B::ROWS * SLOTS + off, stride};
+        const int next = tile + 2 * G;
+        auto hook = [&]() {
+            __syncthreads();  // every thread has its inputs: buffer k is free
+            if (threadIdx.x == 0 && next < t1) {
+                fence_proxy_async_smem();
+                issue(next, k);
+            }
+        };
+        if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
+        else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
+        else tile_y_inv<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
+    }
+}
+
 // ==========================================================================
 // launch helpers and variants
 // ==========================================================================
@@ -650,10 +772,11 @@ template <int PASS, class Cfg, int A, int B> struct SmemTag {};
 // A variant fixes lines per thread and the CTA's target thread count; the
 // tile width (column passes: SLOTS lines, row passes: PAIRS row pairs)
 // follows from the line's thread count T.
-template <int LPT_, int THREADS_, int MINB_ = 1> struct Var {
+template <int LPT_, int THREADS_, int MINB_ = 1, bool TMA_ = false> struct Var {
     static constexpr int LPT = LPT_;
     static constexpr int THREADS = THREADS_;
     static constexpr int MINB = MINB_;  // minimum resident CTAs per SM (register cap)
+    static constexpr bool TMA = TMA_;   // column passes: persistent kernel with TMA prefetch (FP32)
 };
 
 template <class Cfg, class V> constexpr int var_slots() {
@@ -703,9 +826,89 @@ cudaError_t launch_row(int pass, const PassParams<typename Cfg::R>& p, int rows,
     return cudaGetLastError();
 }
 
+// Host side of k_col_tma: tensor map of the pass's input array, grid of at
+// most the resident CTAs, then the narrow tiles (Nyquist column, not a TMA
+// box) through the plain kernel.
+template <int PASS, class Cfg, int S, int L, int MINB>
+cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, int n_wide, cudaStream_t st) {
+    using B = TmaBox<PASS, Cfg, S>;
+    constexpr int NT = col_threads<Cfg, S, L>();
+    constexpr size_t work = PASS == 2 ? col_smem_z<Cfg, S>() : col_smem<Cfg, S>();
+    constexpr size_t sm = B::WORK_OFF + work;
+    cudaError_t e;
+    const int w1 = t_end < n_wide ? t_end : n_wide;
+    if (t_begin < w1) {
+        auto kern = k_col_tma<PASS, Cfg, S, L, MINB>;
+        if ((e = set_smem<SmemTag<40 + PASS, Cfg, S, L * 16 + MINB>>(kern, sm)) != cudaSuccess) return e;
+        static int per_sm[64] = {};  // resident CTAs per SM, per device
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        const int d = dev < 64 ? dev : 63;
+        if (per_sm[d] == 0) {
+            int occ = 0, nsm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, sm)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            per_sm[d] = (occ > 0 ? occ : 1) * nsm;
+        }
+        // input array: W1 [nz][ny][sx] (y forward) or W2 [nz][2ny][sx]
+        const int rows_mid = PASS == 1 ? p.ny : 2 * p.ny;
+        const void* base = PASS == 2 ? p.out : p.in;
+        const unsigned long long dims[3] = {2ull * (unsigned long long)(p.nx + 1), (unsigned long long)rows_mid,
+                                            (unsigned long long)p.nz};
+        const unsigned long long strides[2] = {(unsigned long long)p.sx * 8ull,
+                                               (unsigned long long)p.sx * 8ull * rows_mid};
+        const unsigned box[3] = {2u * B::XW, PASS == 2 ? (unsigned)B::NLW : (unsigned)B::CH,
+                                 PASS == 2 ? (unsigned)B::CH : (unsigned)B::NLW};
+        CUtensorMap map;
+        if ((e = tma_encode_3d_f32(&map, base, dims, strides, box)) != cudaSuccess) return e;
+        const int count = w1 - t_begin;
+        const int grid = count < per_sm[d] ? count : per_sm[d];
+        kern<<<grid, NT, sm, st>>>(p, map, t_begin, w1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int n0 = t_begin > n_wide ? t_begin : n_wide;
+    if (n0 < t_end) {
+        PassParams<float> q = p;
+        q.tile0 = n0;
+        const int grid = t_end - n0;
+        if constexpr (PASS == 1) {
+            if ((e = set_smem<SmemTag<1, Cfg, S, L * 16 + MINB>>(k_y_fwd<Cfg, S, L, MINB>, col_smem<Cfg, S>())))
+                return e;
+            k_y_fwd<Cfg, S, L, MINB><<<grid, NT, col_smem<Cfg, S>(), st>>>(q);
+        } else if constexpr (PASS == 3) {
+            if ((e = set_smem<SmemTag<3, Cfg, S, L * 16 + MINB>>(k_y_inv<Cfg, S, L, MINB>, col_smem<Cfg, S>())))
+                return e;
+            k_y_inv<Cfg, S, L, MINB><<<grid, NT, col_smem<Cfg, S>(), st>>>(q);
+        } else {
+            if ((e = set_smem<SmemTag<2, Cfg, S, L * 16 + MINB>>(k_z_conv<Cfg, S, L, MINB>, col_smem_z<Cfg, S>())))
+                return e;
+            k_z_conv<Cfg, S, L, MINB><<<grid, NT, col_smem_z<Cfg, S>(), st>>>(q);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// wide tiles of a column pass (the ones k_col_tma takes)
+template <class R, int SLOTS> inline int col_wide_tiles(int ncols, int L) {
+    constexpr int XW = SLOTS < Seg<R>::XW ? SLOTS : Seg<R>::XW;
+    constexpr int NLW = SLOTS / XW;
+    return (ncols / XW) * ((L + NLW - 1) / NLW);
+}
+
 template <class Cfg, class V>
 cudaError_t launch_col(int pass, const PassParams<typename Cfg::R>& p, cudaStream_t st) {
     using R = typename Cfg::R;
+    if constexpr (V::TMA && std::is_same<R, float>::value) {
+        constexpr int S = var_slots<Cfg, V>();
+        const int lines = pass == 2 ? 2 * p.ny : p.nz;
+        const int total = col_grid<R, S>(p.nx + 1, lines);
+        const int n_wide = col_wide_tiles<R, S>(p.nx + 1, lines);
+        const int tb = p.tile0, te = p.ntile > 0 ? p.tile0 + p.ntile : total;
+        if (pass == 1) return launch_col_tma<1, Cfg, S, V::LPT, V::MINB>(p, tb, te, n_wide, st);
+        if (pass == 3) return launch_col_tma<3, Cfg, S, V::LPT, V::MINB>(p, tb, te, n_wide, st);
+        return launch_col_tma<2, Cfg, S, V::LPT, V::MINB>(p, tb, te, n_wide, st);
+    }
     constexpr int S = var_slots<Cfg, V>();
     constexpr int L = V::LPT;
     constexpr size_t sm = col_smem<Cfg, S>();

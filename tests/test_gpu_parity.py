@@ -360,7 +360,9 @@ def test_banded_execution_matches_oracle(pg, oracle_mod, shape, mode):
     x = torch.from_numpy(rho).cuda()
     with pg.Plan(nx, ny, nz) as plan:
         counts = plan.info()["variant_count"]
-        for v in (0, 2, 4):  # band ranges follow each pass's tile width
+        # band ranges follow each pass's tile width; the last two column
+        # variants are the persistent TMA kernels, which take band ranges too
+        for v in (0, 2, 4, counts[1] - 2, counts[1] - 1):
             for pss in range(5):
                 plan.set_variant(pss, min(v, counts[pss] - 1))
             plan.set_variant(5, mode)
@@ -368,3 +370,19 @@ def test_banded_execution_matches_oracle(pg, oracle_mod, shape, mode):
                 out = plan.solve(x).double().cpu().numpy()
                 l2, mx = rel_errors(out, ref)
                 assert l2 <= TOL32[0] and mx <= TOL32[1], (v, l2, mx)
+
+
+def test_launch_count_follows_configuration(pg):
+    with pg.Plan(64, 64, 64) as plan:
+        counts = plan.info()["variant_count"]
+        for pss in range(5):
+            plan.set_variant(pss, 0)
+        plan.set_variant(5, 0)
+        assert plan.launch_count() == 5
+        # persistent TMA column kernels add one plain launch for the Nyquist
+        # column (kx = nx) of each column pass
+        for pss in (1, 2, 3):
+            plan.set_variant(pss, counts[pss] - 1)
+        assert plan.launch_count() == 8
+        plan.set_variant(5, 1)  # fused dataflow kernel
+        assert plan.launch_count() == 1
