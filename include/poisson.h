@@ -161,6 +161,23 @@ poisson_status poisson_solve_host(poisson_plan_t plan, const void* rho_host, voi
                                   void* cuda_stream);
 
 /*
+ * Solve count independent fields (e.g. the levels of a nested grid, Section
+ * 3) from host buffers, overlapping the transfers with the solves: level
+ * i's host-to-device copy runs on a copy stream while earlier levels solve
+ * on cuda_stream, and its device-to-host copy on a second copy stream while
+ * later levels solve (the paper stages every level through host memory and
+ * measures those transfers, Section 4).  rho_host[i] / phi_host[i] hold
+ * plans[i]'s grid, dense [z][y][x] in the plan's precision; page-locked host
+ * memory is needed for the copies to overlap (pageable memory works but
+ * serialises).  A plan may appear more than once; its staging buffers (the
+ * ones poisson_solve_host uses) are then reused in order.  Returns when every
+ * phi_host[i] is written.  All plans on one device.  Errors: POISSON_ERR_ARG,
+ * POISSON_ERR_UNSUPPORTED, POISSON_ERR_CUDA, POISSON_ERR_ALLOC.
+ */
+poisson_status poisson_solve_host_levels(poisson_plan_t const* plans, int count, const void* const* rho_host,
+                                         void* const* phi_host, void* cuda_stream);
+
+/*
  * Launch one pass of poisson_solve (pass 0..4: x forward, y forward, z
  * convolve, y inverse, x inverse).  Calling passes 0..4 in order on one
  * stream is exactly poisson_solve; used to time passes individually.

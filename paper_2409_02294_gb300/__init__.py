@@ -12,6 +12,7 @@ Public entry points mirror the C-ABI of ``include/poisson.h``:
   ``.solve_host(rho_host)``, ``.solve_pass(i, rho, phi)``,
   ``.greens_octant()``, ``.info()``, ``.close()``
 * ``solve_batched(plans, rhos, phis)`` - ``poisson_solve_batched``
+* ``solve_host_levels(plans, rhos_host)`` - ``poisson_solve_host_levels``
 * ``PoissonSolve`` - torch.autograd.Function (forward solve, backward adjoint)
 """
 from . import abi  # noqa: F401
@@ -22,7 +23,9 @@ from .abi import (  # noqa: F401
     PoissonSolve,
     lib,
     solve_batched,
+    solve_host_levels,
     supported_size,
 )
 
-__all__ = ["Plan", "PoissonError", "PoissonSolve", "batch_mode", "lib", "solve_batched", "supported_size"]
+__all__ = ["Plan", "PoissonError", "PoissonSolve", "batch_mode", "lib", "solve_batched", "solve_host_levels",
+           "supported_size"]

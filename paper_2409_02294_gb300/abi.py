@@ -53,6 +53,7 @@ SIGNATURES = [
     ("poisson_solve_batched", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("poisson_solve_host", _I, [_P, _P, _P, _P]),
     ("poisson_plan_launch_count", _I, [_P, ctypes.POINTER(_I)]),
+    ("poisson_solve_host_levels", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("poisson_batch_get_mode", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I)]),
     ("poisson_batch_set_mode", _I, [ctypes.POINTER(_P), _I, _I]),
     ("poisson_solve_pass", _I, [_P, _I, _P, _P, _P]),
@@ -256,6 +257,27 @@ def solve_batched(plans, rhos, phis, stream=None):
     op = PA(*[ctypes.c_void_p(o.data_ptr()) for o in phis])
     _check(lib().poisson_solve_batched(hp, n, rp, op, _stream_handle(stream)), "poisson_solve_batched")
     return phis
+
+
+def solve_host_levels(plans, rhos_host, phis_host=None, stream=None):
+    """Solve independent fields from host tensors (pinned for overlap) with
+    the transfers overlapped with the solves (poisson_solve_host_levels)."""
+    torch = _torch()
+    n = len(plans)
+    if phis_host is None:
+        phis_host = [torch.empty_like(r) for r in rhos_host]
+    if len(rhos_host) != n or len(phis_host) != n:
+        raise ValueError("plans, rhos and phis must have the same length")
+    for p, r, o in zip(plans, rhos_host, phis_host):
+        for t in (r, o):
+            if tuple(t.shape) != p.shape or t.dtype != p.dtype or t.is_cuda or not t.is_contiguous():
+                raise ValueError("expected contiguous host %s tensors of shape %s" % (p.dtype, p.shape))
+    PA = ctypes.c_void_p * max(n, 1)
+    hp = PA(*[p.handle for p in plans])
+    rp = PA(*[ctypes.c_void_p(r.data_ptr()) for r in rhos_host])
+    op = PA(*[ctypes.c_void_p(o.data_ptr()) for o in phis_host])
+    _check(lib().poisson_solve_host_levels(hp, n, rp, op, _stream_handle(stream)), "poisson_solve_host_levels")
+    return phis_host
 
 
 def solve_noalloc(rho, h=1.0, G=1.0, out=None, stream=None):

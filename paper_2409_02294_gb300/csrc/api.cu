@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -445,6 +446,83 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, voi
     poisson_status s = check_io(plan, w_dev, grad_dev);
     if (s != POISSON_OK) return s;
     return solve_all(plan, w_dev, grad_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+namespace {
+// Copy streams and events of the overlapped host path, one set per device.
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    std::vector<cudaEvent_t> ev;  // 3 per level: copied in, solved, copied out
+};
+std::mutex g_pipe_mu;
+HostPipe g_pipe[64];
+
+cudaError_t pipe_events(HostPipe& hp, size_t need) {
+    while (hp.ev.size() < need) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r != cudaSuccess) return r;
+        hp.ev.push_back(e);
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
+poisson_status poisson_solve_host_levels(poisson_plan_t const* plans, int count, const void* const* rho_host,
+                                         void* const* phi_host, void* cuda_stream) {
+    if (count < 0 || (count > 0 && (!plans || !rho_host || !phi_host))) return POISSON_ERR_ARG;
+    if (count == 0) return POISSON_OK;
+    for (int i = 0; i < count; ++i)
+        if (!plans[i] || !rho_host[i] || !phi_host[i] || plans[i]->device != plans[0]->device)
+            return POISSON_ERR_ARG;
+    const int dev = plans[0]->device;
+    if (dev < 0 || dev >= 64) return POISSON_ERR_UNSUPPORTED;
+    if (cudaSetDevice(dev) != cudaSuccess) return POISSON_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lock(g_pipe_mu);
+    HostPipe& hp = g_pipe[dev];
+    cudaError_t e;
+    if (!hp.in) {
+        if ((e = cudaStreamCreateWithFlags(&hp.in, cudaStreamNonBlocking))) return cuda_status(e);
+        if ((e = cudaStreamCreateWithFlags(&hp.out, cudaStreamNonBlocking))) return cuda_status(e);
+    }
+    if ((e = pipe_events(hp, 3 * (size_t)count + 1))) return cuda_status(e);
+    cudaEvent_t* ev = hp.ev.data();
+    cudaEvent_t start = ev[3 * count];
+    // the copies start after whatever the caller queued before this call
+    if ((e = cudaEventRecord(start, st))) return cuda_status(e);
+    if ((e = cudaStreamWaitEvent(hp.in, start, 0))) return cuda_status(e);
+    for (int i = 0; i < count; ++i) {
+        poisson_plan_s* pl = plans[i];
+        const size_t bytes = (size_t)pl->nx * pl->ny * pl->nz * pl->rsize;
+        if (!pl->stage_in) {
+            if ((e = cudaMalloc(&pl->stage_in, bytes))) return cuda_status(e);
+            if ((e = cudaMalloc(&pl->stage_out, bytes))) return cuda_status(e);
+        }
+        int prev = -1;  // an earlier level of the same plan: its staging buffers are reused
+        for (int j = i - 1; j >= 0 && prev < 0; --j)
+            if (plans[j] == pl) prev = j;
+        cudaEvent_t in_done = ev[3 * i], solved = ev[3 * i + 1], out_done = ev[3 * i + 2];
+        // copy-in stream: level i's rho, once an earlier solve of this plan has read stage_in
+        if (prev >= 0 && (e = cudaStreamWaitEvent(hp.in, ev[3 * prev + 1], 0))) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(pl->stage_in, rho_host[i], bytes, cudaMemcpyHostToDevice, hp.in)))
+            return cuda_status(e);
+        if ((e = cudaEventRecord(in_done, hp.in))) return cuda_status(e);
+        // caller's stream: the solve, once rho is in and stage_out has been copied out
+        if ((e = cudaStreamWaitEvent(st, in_done, 0))) return cuda_status(e);
+        if (prev >= 0 && (e = cudaStreamWaitEvent(st, ev[3 * prev + 2], 0))) return cuda_status(e);
+        poisson_status s = solve_all(pl, pl->stage_in, pl->stage_out, st);
+        if (s != POISSON_OK) return s;
+        if ((e = cudaEventRecord(solved, st))) return cuda_status(e);
+        // copy-out stream: level i's phi
+        if ((e = cudaStreamWaitEvent(hp.out, solved, 0))) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(phi_host[i], pl->stage_out, bytes, cudaMemcpyDeviceToHost, hp.out)))
+            return cuda_status(e);
+        if ((e = cudaEventRecord(out_done, hp.out))) return cuda_status(e);
+    }
+    for (int i = 0; i < count; ++i)
+        if ((e = cudaStreamWaitEvent(st, ev[3 * i + 2], 0))) return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(st));
 }
 
 poisson_status poisson_solve_pass(poisson_plan_t plan, int pass, const void* rho_dev, void* phi_dev,
