@@ -441,6 +441,19 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
     const int r0 = tile * 2 * PAIRS;
     const int nrows = min(2 * PAIRS, rows - r0);
 
+    cpx<R> v[LPT][E];
+    const bool has_a = 2 * pr < nrows, has_b = 2 * pr + 1 < nrows;
+    if constexpr (LPT == 2) {
+        // both halves in one thread: read x[j], j = t + T m, of the pair's two
+        // rows straight from rho (lanes of consecutive j read consecutive words)
+        const R* __restrict__ xa = static_cast<const R*>(p.in) + (long long)(r0 + 2 * pr) * N;
+        const R* __restrict__ xb = xa + N;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int j = t + T * m;
+            v[0][m] = {has_a ? xa[j] : (R)0, has_b ? xb[j] : (R)0};
+        }
+    } else {
     // stage the tile's rows with 16-byte loads, all issued before any store
     {
         const V* __restrict__ src = reinterpret_cast<const V*>(static_cast<const R*>(p.in) + (long long)r0 * N);
@@ -461,8 +474,6 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
         }
     }
     __syncthreads();
-    cpx<R> v[LPT][E];
-    const bool has_a = 2 * pr < nrows, has_b = 2 * pr + 1 < nrows;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int j = t + T * m;
@@ -471,6 +482,7 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
         v[0][m] = {a, b};
     }
     __syncthreads();  // the staging area becomes the line buffers
+    }
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
@@ -520,9 +532,86 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
 }
 
 // pass 4: C2R along x + crop.  W1 (nx+1 bins) -> phi (real rows of nx).
+// Two adjacent complex values p[0], p[1] (p 16-byte aligned), L1-bypassing
+// when CG.
+template <bool CG, class R> __device__ __forceinline__ void ld_c2(const cpx<R>* p, cpx<R>& a, cpx<R>& b) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 v = CG ? __ldcg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+        a = {v.x, v.y};
+        b = {v.z, v.w};
+    } else {
+        a = ld_c<CG>(p);
+        b = ld_c<CG>(p + 1);
+    }
+}
+
+// pass 4 with both halves in one thread (LPT = 2): every thread reads the
+// spectrum bins it needs straight from W1 (bins 2j and 2j+1 of both rows as
+// 16-byte pairs below the Nyquist bin, mirrored pairs above it; lanes of
+// consecutive j read consecutive pairs), combines the halves in registers
+// and writes its outputs x[j] straight to phi (lanes of consecutive j write
+// consecutive words).  Only the line transform's exchange uses shared memory.
+template <class Cfg, int PAIRS, bool CG>
+__device__ __forceinline__ void tile_x_inv_direct(const PassParams<typename Cfg::R>& p, int rows, int tile,
+                                                   unsigned char* smem_raw) {
+    using R = typename Cfg::R;
+    constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
+    constexpr int LS = row_line_stride<Cfg>();
+    constexpr int SH = RowPad<R>::SHIFT;
+    cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
+    const RowIds<Cfg, PAIRS, 2> id;
+    const int t = id.t, pr = id.pr;
+    const int r0 = tile * 2 * PAIRS;
+    const int nrows = min(2 * PAIRS, rows - r0);
+    const bool has_a = 2 * pr < nrows, has_b = 2 * pr + 1 < nrows;
+    const cpx<R>* __restrict__ in = static_cast<const cpx<R>*>(p.in);
+    const cpx<R>* ra = in + (long long)(r0 + 2 * pr) * p.sx;
+    const cpx<R>* rb = ra + p.sx;
+
+    // Z[k] = A[k] + i B[k]; A[2N-k] = conj A[k] (same for B).  Register line
+    // l holds Z[2j + l], j = t + T m.
+    cpx<R> v[2][E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int k0 = 2 * (t + T * m);
+        cpx<R> a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
+        if (m < E / 2) {  // k0 + 1 < N: the pair (k0, k0 + 1)
+            if (has_a) ld_c2<CG>(ra + k0, a0, a1);
+            if (has_b) ld_c2<CG>(rb + k0, b0, b1);
+            v[0][m] = {a0.x - b0.y, a0.y + b0.x};
+            v[1][m] = {a1.x - b1.y, a1.y + b1.x};
+        } else {          // k0 >= N: bins 2N - k0 and 2N - k0 - 1
+            const int kk = 2 * N - k0;
+            if (has_a) { a0 = ld_c<CG>(ra + kk); a1 = ld_c<CG>(ra + kk - 1); }
+            if (has_b) { b0 = ld_c<CG>(rb + kk); b1 = ld_c<CG>(rb + kk - 1); }
+            v[0][m] = k0 <= N ? cpx<R>{a0.x - b0.y, a0.y + b0.x} : cpx<R>{a0.x + b0.y, b0.x - a0.y};
+            v[1][m] = cpx<R>{a1.x + b1.y, b1.x - a1.y};
+        }
+    }
+    LineSmem<R> ls[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) ls[l] = {sm + (l * PAIRS + pr) * LS, 1, SH, 1};
+    line_fft<R, N, E, true, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
+
+    // x[j] = a[j] + W_2N^-j b[j]: real part -> row 2 pr, imaginary -> row 2 pr + 1
+    R* oa = static_cast<R*>(p.out) + (long long)(r0 + 2 * pr) * N;
+    R* ob = oa + N;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int j = t + T * m;
+        const cpx<R> x = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + j));
+        if (has_a) oa[j] = x.x;
+        if (has_b) ob[j] = x.y;
+    }
+}
+
 template <class Cfg, int PAIRS, int LPT, bool CG>
 __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p, int rows, int tile,
                                             unsigned char* smem_raw) {
+    if constexpr (LPT == 2) {
+        tile_x_inv_direct<Cfg, PAIRS, CG>(p, rows, tile, smem_raw);
+        return;
+    }
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
     constexpr int LS = row_line_stride<Cfg>();
