@@ -71,7 +71,7 @@ template <class R> struct Variants;
 template <> struct Variants<float> {
     using Col = std::tuple<Var<2, 128>, Var<2, 256>, Var<1, 256>, Var<1, 512>, Var<2, 64>,
                            Var<2, 128, 3>, Var<2, 64, 5>, Var<2, 128, 3, true>, Var<1, 256, 2, true>>;
-    using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>, Var<1, 256, 3>>;
+    using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>, Var<1, 256, 3>, Var<2, 64>, Var<2, 128, 4>>;
 };
 template <> struct Variants<double> {
     using Col = std::tuple<Var<1, 256>>;
