@@ -93,6 +93,27 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
                                       int r_near, void* cuda_stream);
 
 /*
+ * Plan for a caller-supplied real kernel that is even along every axis (a
+ * generalisation of the Green's function of Section 3: screened or softened
+ * potentials, smoothing kernels):
+ *     Phi[i] = scale * sum_j k(|i - j|) rho[j],  i, j in [0, n)^3,
+ * where k_octant holds k on the octant, FP64, host memory, dense
+ * [dz][dy][dx] with 0 <= d <= n per axis ((nz+1)(ny+1)(nx+1) values; the
+ * entries at d = n only sit at the padded grid's wrapped index M/2 and never
+ * reach a kept output, but keep the transform real).  The plan copies and
+ * transforms it once (FP64 on the GPU); the caller's array can be freed on
+ * return.  Everything else (precisions, solves, adjoint = the same solve
+ * since the kernel is even, batching, autotuning) is as for
+ * poisson_plan_create; the plan's info reports h = 1, G = 0.
+ * Errors: POISSON_ERR_ARG (null pointers, non-finite values, bad sizes),
+ * POISSON_ERR_UNSUPPORTED (edge length or precision), POISSON_ERR_ALLOC,
+ * POISSON_ERR_CUDA.
+ */
+poisson_status poisson_plan_create_kernel(poisson_plan_t* out, int nx, int ny, int nz, const double* k_octant,
+                                          double scale, poisson_precision prec, unsigned flags,
+                                          void* cuda_stream);
+
+/*
  * Phi = G * rho.  rho_dev: nx*ny*nz input values; phi_dev: nx*ny*nz outputs.
  * rho_dev and phi_dev may be the same buffer (rho is fully consumed before
  * phi is written).  Asynchronous on cuda_stream.  A plan holds one

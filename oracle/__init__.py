@@ -15,13 +15,15 @@ exactly up to rounding, so the oracle is that definition, evaluated three
 independent ways:
 
 1. ``solve_direct``  - the pair sum itself (O(n^6)), tiny grids;
-   ``sample_direct`` - the same sum at chosen target cells, any size.
+   ``sample_direct`` - the same sum at chosen target cells, any size;
+   ``solve_direct_kernel`` - the pair sum with a caller's even kernel.
 2. ``solve_dft``     - zero-pad to M = 2n per axis, apply a dense FP64 DFT
    matrix along each axis (a matmul), multiply by the transformed kernel,
    apply the inverse DFT matrix, crop.  DFT matrix entries are indexed by
    (j*k mod M) from one table of M roots of unity.
 3. ``solve_fft``     - the same padded convolution with a library FP64 FFT
-   (scipy.fft), for full fields at the large sizes.
+   (scipy.fft), for full fields at the large sizes; ``solve_fft_kernel``
+   with a caller's even kernel.
 
 The kernel k(d) and the readings of the paper it rests on are described in
 ``oracle.c``.  Pins of every function here against values fixed by the
@@ -187,6 +189,39 @@ def solve_direct(rho, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT):
     phi = np.empty_like(rho)
     lib().oracle_direct_sum(nx, ny, nz, _ptr(rho), _ptr(koct), -G * hx * hy * hz, _ptr(phi))
     return phi
+
+
+def solve_direct_kernel(rho, k_octant, scale):
+    """Phi[i] = scale sum_j k(|i - j|) rho[j] for a caller's per-axis even
+    kernel given on the octant k_octant[dz, dy, dx], 0 <= d < n per axis
+    (entries beyond are not used), O(n^6)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    koct = np.ascontiguousarray(np.asarray(k_octant, dtype=np.float64)[:nz, :ny, :nx])
+    phi = np.empty_like(rho)
+    lib().oracle_direct_sum(nx, ny, nz, _ptr(rho), _ptr(koct), float(scale), _ptr(phi))
+    return phi
+
+
+def solve_fft_kernel(rho, k_octant, scale, workers=-1):
+    """The padded (M = 2n) FFT convolution with a caller's octant kernel,
+    k_octant[dz, dy, dx] for 0 <= d <= n (entry n fills the wrapped index
+    M/2, which reaches no kept output)."""
+    import scipy.fft as sfft
+    rho = np.asarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    M = (2 * nz, 2 * ny, 2 * nx)
+    koct = np.asarray(k_octant, dtype=np.float64)
+
+    def fold(m):
+        a = np.arange(m)
+        return np.minimum(a, m - a)
+
+    kw = koct[np.ix_(fold(M[0]), fold(M[1]), fold(M[2]))] * float(scale)
+    X = sfft.rfftn(rho, s=M, workers=workers)
+    X *= sfft.rfftn(kw, workers=workers)
+    phi = sfft.irfftn(X, s=M, workers=workers)
+    return np.ascontiguousarray(phi[:nz, :ny, :nx])
 
 
 def sample_direct(rho, targets, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT, koct=None):

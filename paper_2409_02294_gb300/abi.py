@@ -53,6 +53,8 @@ SIGNATURES = [
     ("poisson_solve_batched", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("poisson_solve_host", _I, [_P, _P, _P, _P]),
     ("poisson_plan_launch_count", _I, [_P, ctypes.POINTER(_I)]),
+    ("poisson_plan_create_kernel", _I, [ctypes.POINTER(_P), _I, _I, _I, _P, ctypes.c_double, _I, ctypes.c_uint,
+                                        _P]),
     ("poisson_solve_host_levels", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("poisson_batch_get_mode", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I)]),
     ("poisson_batch_set_mode", _I, [ctypes.POINTER(_P), _I, _I]),
@@ -130,6 +132,27 @@ class Plan:
                                             self.h[0], self.h[1], self.h[2], self.G,
                                             PRECISIONS[precision], int(flags), int(r_near), st),
                "poisson_plan_create")
+
+    @classmethod
+    def from_kernel(cls, k_octant, scale=1.0, precision="fp32", flags=0, stream=None):
+        """Plan for Phi = scale * sum_j k(|i - j|) rho[j] with a caller's real,
+        per-axis even kernel given on the octant: k_octant[dz, dy, dx] for
+        0 <= d <= n (shape (nz+1, ny+1, nx+1)); poisson_plan_create_kernel."""
+        k = np.ascontiguousarray(k_octant, dtype=np.float64)
+        if k.ndim != 3:
+            raise ValueError("k_octant must be 3-D [dz, dy, dx]")
+        nz, ny, nx = (int(v) - 1 for v in k.shape)
+        self = cls.__new__(cls)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.h = (1.0, 1.0, 1.0)
+        self.G = 0.0
+        self.precision = precision
+        self._handle = ctypes.c_void_p()
+        _check(lib().poisson_plan_create_kernel(ctypes.byref(self._handle), nx, ny, nz,
+                                                ctypes.c_void_p(k.ctypes.data), float(scale),
+                                                PRECISIONS[precision], int(flags), _stream_handle(stream)),
+               "poisson_plan_create_kernel")
+        return self
 
     # -- properties ---------------------------------------------------------
     @property

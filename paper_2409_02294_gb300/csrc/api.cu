@@ -353,9 +353,35 @@ const char* poisson_status_string(poisson_status s) {
 
 int poisson_supported_size(int n) { return size_supported(n) ? 1 : 0; }
 
+namespace {
+// Plan creation for the Green's kernel (user_k null) or a caller's kernel.
+poisson_status create_plan(poisson_plan_t* out, int nx, int ny, int nz, double hx, double hy, double hz,
+                           double G, poisson_precision prec, unsigned flags, int r_near, const double* user_k,
+                           double user_scale, void* cuda_stream);
+}  // namespace
+
+poisson_status poisson_plan_create_kernel(poisson_plan_t* out, int nx, int ny, int nz, const double* k_octant,
+                                          double scale, poisson_precision prec, unsigned flags,
+                                          void* cuda_stream) {
+    if (!out) return POISSON_ERR_ARG;
+    *out = nullptr;
+    if (!k_octant || !std::isfinite(scale) || nx <= 0 || ny <= 0 || nz <= 0) return POISSON_ERR_ARG;
+    const size_t n = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(k_octant[i])) return POISSON_ERR_ARG;
+    return create_plan(out, nx, ny, nz, 1.0, 1.0, 1.0, 0.0, prec, flags, 0, k_octant, scale, cuda_stream);
+}
+
 poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int nz, double hx,
                                       double hy, double hz, double G, poisson_precision prec,
                                       unsigned flags, int r_near, void* cuda_stream) {
+    return create_plan(out, nx, ny, nz, hx, hy, hz, G, prec, flags, r_near, nullptr, 0.0, cuda_stream);
+}
+
+namespace {
+poisson_status create_plan(poisson_plan_t* out, int nx, int ny, int nz, double hx, double hy, double hz,
+                           double G, poisson_precision prec, unsigned flags, int r_near, const double* user_k,
+                           double user_scale, void* cuda_stream) {
     if (!out) return POISSON_ERR_ARG;
     *out = nullptr;
     if (!(hx > 0.0) || !(hy > 0.0) || !(hz > 0.0) || !std::isfinite(hx) || !std::isfinite(hy) ||
@@ -405,10 +431,11 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
                                  : upload_twiddles<float>(dims[a], &p->tw[a], st);
         if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
     }
-    const double scale = -G * hx * hy * hz / (8.0 * (double)nx * (double)ny * (double)nz);
+    // the inverse transform's 1/(Mx My Mz) is folded into Ghat
+    const double scale = (user_k ? user_scale : -G * hx * hy * hz) / (8.0 * (double)nx * (double)ny * (double)nz);
     e = build_greens(nx, ny, nz, hx, hy, hz, r_near, scale,
                      prec == POISSON_FP64 ? nullptr : static_cast<float*>(p->greens),
-                     prec == POISSON_FP64 ? static_cast<double*>(p->greens) : nullptr, st);
+                     prec == POISSON_FP64 ? static_cast<double*>(p->greens) : nullptr, st, user_k);
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
     if (flags & POISSON_FLAG_AUTOTUNE) {
         poisson_status s = autotune(p, st);
@@ -417,6 +444,7 @@ poisson_status poisson_plan_create_ex(poisson_plan_t* out, int nx, int ny, int n
     *out = p;
     return POISSON_OK;
 }
+}  // namespace
 
 poisson_status poisson_plan_create(poisson_plan_t* out, int nx, int ny, int nz, double hx, double hy,
                                    double hz, double G, poisson_precision prec, unsigned flags,

@@ -186,7 +186,8 @@ cudaError_t build_kernel_octant(int nx, int ny, int nz, double hx, double hy, do
 }
 
 cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz, int r_near,
-                         double scale, float* out_f32, double* out_f64, cudaStream_t st) {
+                         double scale, float* out_f32, double* out_f64, cudaStream_t st,
+                         const double* user_octant) {
     const int ex = nx + 1, ey = ny + 1, ez = nz + 1;
     const long long total = (long long)ex * ey * ez;
     double *k0 = nullptr, *k1 = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
@@ -208,7 +209,12 @@ cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz
         if ((err = cudaMemcpyAsync(cx, hcx.data(), hcx.size() * sizeof(double), cudaMemcpyHostToDevice, st))) break;
         if ((err = cudaMemcpyAsync(cy, hcy.data(), hcy.size() * sizeof(double), cudaMemcpyHostToDevice, st))) break;
         if ((err = cudaMemcpyAsync(cz, hcz.data(), hcz.size() * sizeof(double), cudaMemcpyHostToDevice, st))) break;
-        if ((err = build_kernel_octant(nx, ny, nz, hx, hy, hz, r_near, k0, st))) break;
+        if (user_octant) {  // a caller's kernel octant (host memory) instead of the Green's kernel
+            if ((err = cudaMemcpyAsync(k0, user_octant, total * sizeof(double), cudaMemcpyHostToDevice, st)))
+                break;
+        } else if ((err = build_kernel_octant(nx, ny, nz, hx, hy, hz, r_near, k0, st))) {
+            break;
+        }
 
         // x: k1[zy][q] = sum_d k0[zy][d] Cx[q][d]
         GemmDesc g{};

@@ -20,9 +20,12 @@ cudaError_t launch_z_f32(int N, int pass, int var, const PassParams<float>& p, c
 
 // Build the transformed Green's function octant on the device (FP64
 // throughout), scaled by `scale`, written as float (out_f32) or double
-// (out_f64; exactly one of the two is non-null).
+// (out_f64; exactly one of the two is non-null).  With user_octant (host,
+// (nz+1)(ny+1)(nx+1) FP64 values k[dz][dy][dx]) that kernel is transformed
+// instead of the Green's kernel (h and r_near are then unused).
 cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz, int r_near,
-                         double scale, float* out_f32, double* out_f64, cudaStream_t st);
+                         double scale, float* out_f32, double* out_f64, cudaStream_t st,
+                         const double* user_octant = nullptr);
 
 // Raw Green's kernel k(d) octant (FP64, (nx+1)(ny+1)(nz+1)), for tests.
 cudaError_t build_kernel_octant(int nx, int ny, int nz, double hx, double hy, double hz,

@@ -346,3 +346,62 @@ def test_planted_mistakes_fail_a_pin(oracle_mod, which, tmp_path):
     finally:
         oracle_mod.use_library(None)
     assert _pins_pass(oracle_mod)
+
+
+# ---------------------------------------------------------------------------
+# caller-supplied even kernels (generalisation of the Green's function)
+# ---------------------------------------------------------------------------
+
+def _even_kernel(shape_zyx, seed):
+    """A random octant k[dz, dy, dx] (any values: evenness is by construction)."""
+    return np.random.default_rng(seed).standard_normal(shape_zyx)
+
+
+def test_user_kernel_delta_and_constant_closed_forms(oracle_mod):
+    rng = np.random.default_rng(11)
+    rho = rng.standard_normal((5, 6, 7))
+    delta = np.zeros((6, 7, 8))
+    delta[0, 0, 0] = 1.0
+    # k = delta: Phi = scale * rho exactly (direct) and to rounding (FFT)
+    assert np.array_equal(oracle_mod.solve_direct_kernel(rho, delta, 2.5), 2.5 * rho)
+    np.testing.assert_allclose(oracle_mod.solve_fft_kernel(rho, delta, 2.5), 2.5 * rho, rtol=0, atol=1e-13)
+    # k = 1: Phi[i] = scale * sum(rho) at every cell
+    ones = np.ones((6, 7, 8))
+    want = np.full(rho.shape, -0.75 * rho.sum())
+    np.testing.assert_allclose(oracle_mod.solve_direct_kernel(rho, ones, -0.75), want, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(oracle_mod.solve_fft_kernel(rho, ones, -0.75), want, rtol=1e-12, atol=1e-12)
+
+
+def test_user_kernel_brute_force_and_route_agreement(oracle_mod):
+    # brute force in plain Python loops on a tiny grid, then the two routes
+    rng = np.random.default_rng(12)
+    nz, ny, nx = 3, 4, 5
+    rho = rng.standard_normal((nz, ny, nx))
+    k = _even_kernel((nz + 1, ny + 1, nx + 1), 13)
+    brute = np.zeros_like(rho)
+    for iz in range(nz):
+        for iy in range(ny):
+            for ix in range(nx):
+                s = 0.0
+                for jz in range(nz):
+                    for jy in range(ny):
+                        for jx in range(nx):
+                            s += k[abs(iz - jz), abs(iy - jy), abs(ix - jx)] * rho[jz, jy, jx]
+                brute[iz, iy, ix] = 1.5 * s
+    np.testing.assert_allclose(oracle_mod.solve_direct_kernel(rho, k, 1.5), brute, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(oracle_mod.solve_fft_kernel(rho, k, 1.5), brute, rtol=1e-12, atol=1e-12)
+    # larger grid: direct sum = FFT route
+    rho = rng.standard_normal((9, 10, 12))
+    k = _even_kernel((10, 11, 13), 14)
+    a = oracle_mod.solve_direct_kernel(rho, k, 0.5)
+    b = oracle_mod.solve_fft_kernel(rho, k, 0.5)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+def test_user_kernel_with_the_greens_octant_is_the_poisson_solve(oracle_mod):
+    rho = np.random.default_rng(15).standard_normal((6, 7, 8))
+    h = (1.0, 0.5, 2.0)
+    koct = oracle_mod.kernel_octant((9, 8, 7), h=h)  # extents x, y, z = n + 1
+    a = oracle_mod.solve_direct_kernel(rho, koct, -1.0 * 1.0 * 0.5 * 2.0)
+    b = oracle_mod.solve_direct(rho, h=h)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
