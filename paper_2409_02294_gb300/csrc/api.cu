@@ -124,6 +124,7 @@ PassParams<R> pass_params_t(const poisson_plan_s* pl, int pass, const void* rho,
     p.sx = pl->sx;
     p.status = pl->status;
     p.greens = static_cast<const R*>(pl->greens);
+    p.check_finite = pass == 4 && (pl->flags & POISSON_FLAG_CHECK_FINITE) != 0;
     switch (pass) {
         case 0: p.in = rho; p.out = pl->w1; N = pl->nx; p.tw = static_cast<const cpx<R>*>(pl->tw[0]); break;
         case 1: p.in = pl->w1; p.out = pl->w2; N = pl->ny; p.tw = static_cast<const cpx<R>*>(pl->tw[1]); break;

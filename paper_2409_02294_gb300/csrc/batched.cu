@@ -246,6 +246,7 @@ PassParams<float> pass_params(const poisson_plan_s* pl, int pass) {
     p.sx = pl->sx;
     p.status = pl->status;
     p.greens = static_cast<const float*>(pl->greens);
+    p.check_finite = pass == 4 && (pl->flags & POISSON_FLAG_CHECK_FINITE) != 0;
     switch (pass) {
         case 0: p.in = nullptr; p.out = pl->w1; p.tw = static_cast<const cpx<float>*>(pl->tw[0]); break;
         case 1: p.in = pl->w1; p.out = pl->w2; p.tw = static_cast<const cpx<float>*>(pl->tw[1]); break;

@@ -44,7 +44,14 @@ template <class R> struct PassParams {
     unsigned* status;         // device status word (unused by these passes)
     int tile0;                // first tile of this launch (column passes)
     int ntile;                // tiles in this launch, 0 = all
+    int check_finite;         // x inverse: set bit 0 of *status if an output is not finite
 };
+
+// Record a non-finite output in the status word (POISSON_FLAG_CHECK_FINITE).
+template <class R> __device__ __forceinline__ bool not_finite(R v) { return !isfinite(v); }
+__device__ __forceinline__ void flag_non_finite(unsigned* status, bool bad) {
+    if (bad && status) atomicOr(status, 1u);
+}
 
 // bytes of one 128-byte segment in complex elements
 template <class R> struct Seg { static constexpr int XW = 128 / (int)sizeof(cpx<R>); };
@@ -596,13 +603,16 @@ __device__ __forceinline__ void tile_x_inv_direct(const PassParams<typename Cfg:
     // x[j] = a[j] + W_2N^-j b[j]: real part -> row 2 pr, imaginary -> row 2 pr + 1
     R* oa = static_cast<R*>(p.out) + (long long)(r0 + 2 * pr) * N;
     R* ob = oa + N;
+    bool bad = false;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int j = t + T * m;
         const cpx<R> x = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + j));
         if (has_a) oa[j] = x.x;
         if (has_b) ob[j] = x.y;
+        bad |= (has_a && not_finite(x.x)) || (has_b && not_finite(x.y));
     }
+    if (p.check_finite) flag_non_finite(p.status, bad);
 }
 
 template <class Cfg, int PAIRS, int LPT, bool CG>
@@ -697,12 +707,15 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
     }
     __syncthreads();  // line buffers become the output staging area
     if (holder) {
+        bool bad = false;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + T * m;
             stage[(2 * pr) * RS + j] = v[0][m].x;
             stage[(2 * pr + 1) * RS + j] = v[0][m].y;
+            bad |= (has_a && not_finite(v[0][m].x)) || (has_b && not_finite(v[0][m].y));
         }
+        if (p.check_finite) flag_non_finite(p.status, bad);
     }
     __syncthreads();
     {

@@ -386,3 +386,20 @@ def test_launch_count_follows_configuration(pg):
         assert plan.launch_count() == 8
         plan.set_variant(5, 1)  # fused dataflow kernel
         assert plan.launch_count() == 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_check_finite_flag_reports_non_finite_output(pg, precision):
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    rho = torch.zeros((32, 32, 48), device="cuda", dtype=dt)
+    rho[3, 4, 5] = float("nan")
+    with pg.Plan(48, 32, 32, precision=precision, flags=pg.abi.FLAG_CHECK_FINITE) as plan:
+        for v in range(plan.info()["variant_count"][4]):  # staged and direct x inverse
+            plan.set_variant(4, v)
+            plan.solve(rho)
+            assert plan.sync_status() == 6  # POISSON_ERR_NUMERIC
+            plan.solve(torch.ones_like(rho))
+            assert plan.sync_status() == 0
+    with pg.Plan(48, 32, 32, precision=precision) as plan:  # without the flag nothing is checked
+        plan.solve(rho)
+        assert plan.sync_status() == 0
