@@ -35,8 +35,8 @@
 
 namespace pgb {
 
-constexpr int BATCH_THREADS = 256;
-using BatchVar = Var<1, BATCH_THREADS>;
+constexpr int BATCH_THREADS = 128;
+using BatchVar = Var<2, BATCH_THREADS>;  // both halves of a line per thread, as the standalone kernels
 
 struct BatchField {
     PassParams<float> p[5];
@@ -64,8 +64,8 @@ template <int N> struct BatchShape {
     using C = typename SizeCfg<float, N>::C;
     static constexpr int S = var_slots<C, BatchVar>();
     static constexpr int P = var_pairs<C, BatchVar>();
-    static_assert(col_threads<C, S, 1>() == BATCH_THREADS, "column tile must use 256 threads");
-    static_assert(row_threads<C, P, 1>() == BATCH_THREADS, "row tile must use 256 threads");
+    static_assert(col_threads<C, S, 2>() == BATCH_THREADS, "column tile must use BATCH_THREADS threads");
+    static_assert(row_threads<C, P, 2>() == BATCH_THREADS, "row tile must use BATCH_THREADS threads");
     static constexpr size_t smem = col_smem_z<C, S>() > row_smem<C, P>() ? col_smem_z<C, S>() : row_smem<C, P>();
 };
 
@@ -75,11 +75,11 @@ __device__ __noinline__ void batch_tile(int pass, const PassParams<float>& p, in
     using C = typename BatchShape<N>::C;
     constexpr int S = BatchShape<N>::S, P = BatchShape<N>::P;
     switch (pass) {
-        case 0: tile_x_fwd<C, P, 1, true>(p, rows, tile, sm); break;
-        case 1: tile_y_fwd<C, S, 1, true>(p, tile, sm); break;
-        case 2: tile_z_conv<C, S, 1, true>(p, tile, sm); break;
-        case 3: tile_y_inv<C, S, 1, true>(p, tile, sm); break;
-        default: tile_x_inv<C, P, 1, true>(p, rows, tile, sm); break;
+        case 0: tile_x_fwd<C, P, 2, true>(p, rows, tile, sm); break;
+        case 1: tile_y_fwd<C, S, 2, true>(p, tile, sm); break;
+        case 2: tile_z_conv<C, S, 2, true>(p, tile, sm); break;
+        case 3: tile_y_inv<C, S, 2, true>(p, tile, sm); break;
+        default: tile_x_inv<C, P, 2, true>(p, rows, tile, sm); break;
     }
 }
 
@@ -101,15 +101,24 @@ __device__ bool wait_count(const unsigned* ctr, unsigned target, const BatchArgs
     return false;
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched(BatchArgs a) {
+// Thread 0 claims the CTA's next item while the current one runs (a claim
+// only ever comes after the CTA's current item in the queue, so the
+// argument above still holds), and remembers the last (field, pass)
+// dependency it saw complete, so the following tiles of that pass skip the
+// poll.
+__global__ void __launch_bounds__(BATCH_THREADS, 3) k_batched(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_ok;
+    unsigned next = 0;  // thread 0: the item claimed for after the current one
+    int dep_done = -1;  // thread 0: field * 5 + pass of the last counter seen complete
+    if (threadIdx.x == 0) next = atomicAdd(a.ctl, 1u);
     for (;;) {
         __syncthreads();  // the previous tile is done with shared memory
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.ctl, 1u);
+        if (threadIdx.x == 0) s_item = (int)next;
         __syncthreads();
         const int w = s_item;
         if (w >= a.total) return;
+        if (threadIdx.x == 0) next = atomicAdd(a.ctl, 1u);
         // segment holding work item w (segments are sorted by begin)
         int lo = 0, hi = a.nseg - 1;
         while (lo < hi) {
@@ -121,10 +130,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched(BatchArgs a) {
         const BatchField& f = a.fields[sg.field];
         if (threadIdx.x == 0) {
             bool ok = true;
-            if (sg.pass > 0) {
+            const int key = sg.field * 5 + sg.pass - 1;
+            if (sg.pass > 0 && key != dep_done) {
                 unsigned target = (unsigned)f.ntiles[sg.pass - 1];
-                if (sg.field == a.hold_field && sg.pass == 1) target += 1u;  // test hook
-                ok = wait_count(a.ctl + 2 + sg.field * 5 + sg.pass - 1, target, a);
+                const bool held = sg.field == a.hold_field && sg.pass == 1;
+                if (held) target += 1u;  // test hook
+                ok = wait_count(a.ctl + 2 + key, target, a);
+                if (ok && !held) dep_done = key;
             }
             s_ok = ok ? 1 : 0;
         }
@@ -159,18 +171,25 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched(BatchArgs a) {
 // ---------------------------------------------------------------------------
 namespace {
 
-size_t batch_smem() {
+// shared memory of the largest tile among the edge lengths present
+size_t shape_smem(int N) {
+    switch (N) {
+        case 16: return BatchShape<16>::smem;
+        case 32: return BatchShape<32>::smem;
+        case 48: return BatchShape<48>::smem;
+        case 64: return BatchShape<64>::smem;
+        case 96: return BatchShape<96>::smem;
+        case 128: return BatchShape<128>::smem;
+        case 192: return BatchShape<192>::smem;
+        case 256: return BatchShape<256>::smem;
+        case 384: return BatchShape<384>::smem;
+        default: return BatchShape<512>::smem;
+    }
+}
+size_t batch_smem(const std::vector<poisson_plan_t>& plans) {
     size_t m = 0;
-    m = std::max(m, BatchShape<16>::smem);
-    m = std::max(m, BatchShape<32>::smem);
-    m = std::max(m, BatchShape<48>::smem);
-    m = std::max(m, BatchShape<64>::smem);
-    m = std::max(m, BatchShape<96>::smem);
-    m = std::max(m, BatchShape<128>::smem);
-    m = std::max(m, BatchShape<192>::smem);
-    m = std::max(m, BatchShape<256>::smem);
-    m = std::max(m, BatchShape<384>::smem);
-    m = std::max(m, BatchShape<512>::smem);
+    for (const poisson_plan_s* pl : plans)
+        m = std::max({m, shape_smem(pl->nx), shape_smem(pl->ny), shape_smem(pl->nz)});
     return m;
 }
 
@@ -300,7 +319,7 @@ cudaError_t build_state(BatchState* b) {
     if ((e = cudaMalloc(&b->d_ctl, b->ctl_bytes))) return e;
 
     // launch shape: as many CTAs as fit on the GPU at once
-    const size_t smem = batch_smem();
+    const size_t smem = batch_smem(b->plans);
     if ((e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     int per_sm = 0, sms = 0;
