@@ -646,23 +646,36 @@ def run_ours(args):
             libs[k] = v
         host_xfer = host_transfer_experiment()
 
-    # end to end through the C-ABI host-buffer call: H2D + solve + D2H per step
+    # end to end through the C-ABI host-buffer calls: every step's H2D of rho
+    # and D2H of phi are inside the timed region.  The K steps go through one
+    # poisson_solve_host_levels call (each step's transfers overlap the
+    # neighbouring steps' solves); one synchronous poisson_solve_host per step
+    # is reported beside it.
     e2e = None
     if not args.no_e2e:
         host_in = torch.from_numpy(rhos32[0]).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        for _ in range(3):
-            plan.solve_host(host_in, host_out, stream)
         ksteps = max(3, min(args.steps, 50))
+        lv = ([plan] * ksteps, [host_in] * ksteps, [host_out] * ksteps)
+        for _ in range(2):
+            pg.solve_host_levels(*lv, stream=stream)
+            plan.solve_host(host_in, host_out, stream)
+        barrier()
+        t0 = time.perf_counter()
+        pg.solve_host_levels(*lv, stream=stream)
+        te = time.perf_counter() - t0
+        te = max_over_ranks(te, world, dev)
         barrier()
         t0 = time.perf_counter()
         for _ in range(ksteps):
             plan.solve_host(host_in, host_out, stream)
-        te = time.perf_counter() - t0
-        te = max_over_ranks(te, world, dev)
+        ts = time.perf_counter() - t0
+        ts = max_over_ranks(ts, world, dev)
         e2e = {"value": weak_scaling_value(world, n ** 3, ksteps, te), "unit": UNIT,
                "h2d_bytes_per_step": rho32.nbytes, "d2h_bytes_per_step": rho32.nbytes,
-               "steps": ksteps, "host_memory": "pinned"}
+               "steps": ksteps, "host_memory": "pinned",
+               "host_path": "poisson_solve_host_levels over the steps' fields (transfers overlapped)",
+               "synchronous_per_step_value": weak_scaling_value(world, n ** 3, ksteps, ts)}
         if rank == 0 and world == 1:
             pg_in = torch.from_numpy(rhos32[0].copy())
             pg_out = torch.empty_like(pg_in)

@@ -190,8 +190,9 @@ poisson_status poisson_solve_host(poisson_plan_t plan, const void* rho_host, voi
  * measures those transfers, Section 4).  rho_host[i] / phi_host[i] hold
  * plans[i]'s grid, dense [z][y][x] in the plan's precision; page-locked host
  * memory is needed for the copies to overlap (pageable memory works but
- * serialises).  A plan may appear more than once; its staging buffers (the
- * ones poisson_solve_host uses) are then reused in order.  Returns when every
+ * serialises).  A plan may appear more than once (e.g. a stream of fields
+ * of one size): its occurrences alternate between two device staging pairs,
+ * so one level's copies overlap the neighbouring levels' solves.  Returns when every
  * phi_host[i] is written.  All plans on one device.  Errors: POISSON_ERR_ARG,
  * POISSON_ERR_UNSUPPORTED, POISSON_ERR_CUDA, POISSON_ERR_ALLOC.
  */

@@ -88,6 +88,8 @@ void free_plan(poisson_plan_s* p) {
     cudaFree(p->status);
     cudaFree(p->stage_in);
     cudaFree(p->stage_out);
+    cudaFree(p->stage_in2);
+    cudaFree(p->stage_out2);
     cudaFree(p->fused_order);
     cudaFree(p->fused_ctl);
     if (p->band_ready) {
@@ -524,28 +526,35 @@ poisson_status poisson_solve_host_levels(poisson_plan_t const* plans, int count,
     for (int i = 0; i < count; ++i) {
         poisson_plan_s* pl = plans[i];
         const size_t bytes = (size_t)pl->nx * pl->ny * pl->nz * pl->rsize;
-        if (!pl->stage_in) {
-            if ((e = cudaMalloc(&pl->stage_in, bytes))) return cuda_status(e);
-            if ((e = cudaMalloc(&pl->stage_out, bytes))) return cuda_status(e);
+        // earlier levels of the same plan: occurrences alternate between two
+        // staging pairs, so a level's copies overlap its neighbours' solves;
+        // prev is the last earlier level that used the same pair
+        int occ = 0, prev = -1;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == pl) ++occ;
+        for (int j = i - 1, seen = 0; j >= 0 && prev < 0; --j)
+            if (plans[j] == pl && ++seen == 2) prev = j;
+        void** sin = (occ & 1) ? &pl->stage_in2 : &pl->stage_in;
+        void** sout = (occ & 1) ? &pl->stage_out2 : &pl->stage_out;
+        if (!*sin) {
+            if ((e = cudaMalloc(sin, bytes))) return cuda_status(e);
+            if ((e = cudaMalloc(sout, bytes))) return cuda_status(e);
         }
-        int prev = -1;  // an earlier level of the same plan: its staging buffers are reused
-        for (int j = i - 1; j >= 0 && prev < 0; --j)
-            if (plans[j] == pl) prev = j;
         cudaEvent_t in_done = ev[3 * i], solved = ev[3 * i + 1], out_done = ev[3 * i + 2];
-        // copy-in stream: level i's rho, once an earlier solve of this plan has read stage_in
+        // copy-in stream: level i's rho, once the earlier solve from this pair has read it
         if (prev >= 0 && (e = cudaStreamWaitEvent(hp.in, ev[3 * prev + 1], 0))) return cuda_status(e);
-        if ((e = cudaMemcpyAsync(pl->stage_in, rho_host[i], bytes, cudaMemcpyHostToDevice, hp.in)))
+        if ((e = cudaMemcpyAsync(*sin, rho_host[i], bytes, cudaMemcpyHostToDevice, hp.in)))
             return cuda_status(e);
         if ((e = cudaEventRecord(in_done, hp.in))) return cuda_status(e);
-        // caller's stream: the solve, once rho is in and stage_out has been copied out
+        // caller's stream: the solve, once rho is in and this pair's phi has been copied out
         if ((e = cudaStreamWaitEvent(st, in_done, 0))) return cuda_status(e);
         if (prev >= 0 && (e = cudaStreamWaitEvent(st, ev[3 * prev + 2], 0))) return cuda_status(e);
-        poisson_status s = solve_all(pl, pl->stage_in, pl->stage_out, st);
+        poisson_status s = solve_all(pl, *sin, *sout, st);
         if (s != POISSON_OK) return s;
         if ((e = cudaEventRecord(solved, st))) return cuda_status(e);
         // copy-out stream: level i's phi
         if ((e = cudaStreamWaitEvent(hp.out, solved, 0))) return cuda_status(e);
-        if ((e = cudaMemcpyAsync(phi_host[i], pl->stage_out, bytes, cudaMemcpyDeviceToHost, hp.out)))
+        if ((e = cudaMemcpyAsync(phi_host[i], *sout, bytes, cudaMemcpyDeviceToHost, hp.out)))
             return cuda_status(e);
         if ((e = cudaEventRecord(out_done, hp.out))) return cuda_status(e);
     }

@@ -23,6 +23,8 @@ struct poisson_plan_s {
     unsigned* status;     // device status word
     void* stage_in;       // device staging for poisson_solve_host
     void* stage_out;
+    void* stage_in2;      // second staging pair: repeated levels of one plan alternate
+    void* stage_out2;
     int var[5];           // kernel variant per pass (autotuned or default)
     int use_fused;        // 1: one persistent dataflow kernel instead of five launches
     void* fused_order;    // its work queue ((pass, tile) pairs) and counters
