@@ -51,3 +51,15 @@ def test_levels_reject_bad_arguments(pg):
         with pytest.raises(ValueError):
             pg.solve_host_levels([p], [torch.zeros((16, 32, 32))])
     assert pg.solve_host_levels([], []) == []
+
+
+def test_one_plan_repeated_alternates_staging(pg):
+    # five fields through one plan: occurrences alternate between two staging
+    # pairs and reuse each pair after the field two before it
+    with pg.Plan(64, 32, 48) as p:
+        rhos = [torch.from_numpy(workloads.gaussian_blobs(p.shape, count=4, seed=400 + i)[0]
+                                 .astype(np.float32)).pin_memory() for i in range(5)]
+        outs = [torch.empty_like(r).pin_memory() for r in rhos]
+        pg.solve_host_levels([p] * 5, rhos, outs)
+        for r, o in zip(rhos, outs):
+            assert torch.equal(o, p.solve_host(r))
