@@ -60,7 +60,7 @@ typedef enum {
 
 /* plan flags */
 #define POISSON_FLAG_CHECK_FINITE 0x1u /* solves set POISSON_ERR_NUMERIC on NaN/Inf output */
-#define POISSON_FLAG_AUTOTUNE 0x2u     /* run poisson_plan_autotune inside plan creation */
+#define POISSON_FLAG_AUTOTUNE 0x2u     /* tune in plan creation (or reuse this process's result for the shape) */
 
 /* Default Chebyshev radius (in cells) inside which k(d) is the cell average. */
 #define POISSON_R_NEAR_DEFAULT 8
@@ -137,14 +137,17 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, voi
 /*
  * Solve `count` independent fields, plans[i] applied to rho_dev[i] ->
  * phi_dev[i].  Plans may have different sizes but must share the device
- * and precision (FP32).  Two executions exist, each replayed from a CUDA
+ * and precision (FP32).  Three executions exist, each replayed from a CUDA
  * graph: (0) one persistent kernel over the tiles of all fields, with
- * bounded per-field dependency waits; (1) every field's own five kernels,
- * captured into one graph that spreads the fields over four streams.  The
- * first call with a given plan list builds both, times them on the caller's
- * data (synchronising cuda_stream) and keeps the faster; the environment
- * variable POISSON_BATCH_MODE=0 or 1 forces one.  Later calls replay the
- * chosen graph (mode 1 re-captures when the buffers change).  The arrays of
+ * bounded per-field dependency waits; (1) every field's own five kernels
+ * with each plan's own (possibly autotuned) variants, captured into one
+ * graph that spreads the fields over four streams; (2) the same with the
+ * variants plans use untuned (a field's best variants alone on the GPU are
+ * not always the best when fields share it).  The first call with a given
+ * plan list builds all three, times them on the caller's data
+ * (synchronising cuda_stream) and keeps the fastest; the environment
+ * variable POISSON_BATCH_MODE=0, 1 or 2 forces one.  Later calls replay the
+ * chosen graph (modes 1 and 2 re-capture when the buffers change).  The arrays of
  * pointers are host arrays.  Errors: POISSON_ERR_ARG, POISSON_ERR_UNSUPPORTED
  * (mixed precision or devices), POISSON_ERR_CUDA, POISSON_ERR_TIMEOUT
  * (reported by poisson_plan_sync_status on plans[0]).
@@ -164,7 +167,8 @@ poisson_status poisson_plan_launch_count(poisson_plan_t plan, int* launches);
 /*
  * Execution mode of the batch cached for this plan list (after a first
  * poisson_solve_batched call with it): 0 persistent kernel, 1 per-field
- * launches, -1 not decided yet.  set_mode = -1 makes the next call time both
+ * launches with each plan's variants, 2 per-field launches with the untuned
+ * variants, -1 not decided yet.  set_mode = -1 makes the next call time both
  * again.  Errors: POISSON_ERR_ARG (bad arguments, or set_mode on a plan list
  * that has no cached batch yet).
  */
@@ -231,12 +235,16 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
 
 /*
  * Autotuner: for each of the five passes, time every compiled kernel variant
- * (lines per thread, CTA shape) on the plan's own buffers (two warm-up and
- * five timed launches each, CUDA events on cuda_stream) and keep the
- * fastest, then (cubic FP32 grids) times five launches against the fused
- * persistent kernel and keeps the faster mode.  Synchronises cuda_stream;
- * allocates two temporary grid-sized buffers.  Errors: POISSON_ERR_ARG,
- * POISSON_ERR_ALLOC, POISSON_ERR_CUDA.
+ * (lines per thread, CTA shape, register cap, persistent TMA column kernels)
+ * on the plan's own buffers (two warm-up and five timed launches each, CUDA
+ * events on cuda_stream) and keep the fastest, then time the execution modes
+ * (five launches; FP32: banded streams; cubic FP32: the fused persistent
+ * kernel) and keep the fastest.  The result is also recorded for the plan's
+ * shape, precision and device: a later plan created with
+ * POISSON_FLAG_AUTOTUNE for the same shape in this process takes it without
+ * timing again.  Synchronises cuda_stream; allocates two temporary
+ * grid-sized buffers.  Errors: POISSON_ERR_ARG, POISSON_ERR_ALLOC,
+ * POISSON_ERR_CUDA.
  */
 poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream);
 

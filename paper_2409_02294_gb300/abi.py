@@ -328,7 +328,9 @@ def _plan_array(plans):
 
 def batch_mode(plans, mode=None):
     """Get (mode=None) or set the execution mode of the batch cached for
-    this plan list: 0 persistent kernel, 1 per-field launches, -1 undecided."""
+    this plan list: 0 persistent kernel, 1 per-field launches with each
+    plan's variants, 2 per-field launches with the untuned variants, -1
+    undecided."""
     hp = _plan_array(plans)
     if mode is None:
         out = ctypes.c_int(-1)

@@ -169,6 +169,41 @@ int default_variant(poisson_precision prec, int pass) {
 
 // Time every variant of every pass on the plan's own buffers and keep the
 // fastest (minimum of 5 timed launches after two warm-up launches each).
+// Autotune results per (grid, precision, device), shared by every plan of
+// the process: POISSON_FLAG_AUTOTUNE on a shape that was tuned before reuses
+// the result instead of timing again (a batch of many fields with a few
+// distinct shapes tunes each shape once).  poisson_plan_autotune always
+// re-times and refreshes the entry.
+struct TuneEntry {
+    int nx, ny, nz, prec, device;
+    int var[5];
+    int mode;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune_cache;
+
+bool tune_lookup(const poisson_plan_s* pl, TuneEntry* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneEntry& t : g_tune_cache)
+        if (t.nx == pl->nx && t.ny == pl->ny && t.nz == pl->nz && t.prec == (int)pl->prec &&
+            t.device == pl->device) {
+            *out = t;
+            return true;
+        }
+    return false;
+}
+void tune_store(const poisson_plan_s* pl) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    TuneEntry t{pl->nx, pl->ny, pl->nz, (int)pl->prec, pl->device, {}, pl->use_fused};
+    for (int i = 0; i < 5; ++i) t.var[i] = pl->var[i];
+    for (TuneEntry& c : g_tune_cache)
+        if (c.nx == t.nx && c.ny == t.ny && c.nz == t.nz && c.prec == t.prec && c.device == t.device) {
+            c = t;
+            return;
+        }
+    g_tune_cache.push_back(t);
+}
+
 poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
     const size_t cells = (size_t)pl->nx * pl->ny * pl->nz;
     void *rho = nullptr, *phi = nullptr;
@@ -334,9 +369,14 @@ poisson_status solve_all(poisson_plan_t plan, const void* in, void* out, cudaStr
 }  // namespace
 
 namespace pgb {
-cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st) {
-    return run_pass(pl, pass, rho, phi, st);
+cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st,
+                          int var) {
+    if (var < 0) return run_pass(pl, pass, rho, phi, st);
+    poisson_plan_s tmp = *pl;  // the same plan with one pass's variant replaced
+    tmp.var[pass] = var;
+    return run_pass(&tmp, pass, rho, phi, st);
 }
+int plan_default_variant(const poisson_plan_s* pl, int pass) { return default_variant(pl->prec, pass); }
 }  // namespace pgb
 
 extern "C" {
@@ -441,8 +481,19 @@ poisson_status create_plan(poisson_plan_t* out, int nx, int ny, int nz, double h
                      prec == POISSON_FP64 ? static_cast<double*>(p->greens) : nullptr, st, user_k);
     if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
     if (flags & POISSON_FLAG_AUTOTUNE) {
-        poisson_status s = autotune(p, st);
-        if (s != POISSON_OK) { free_plan(p); return s; }
+        TuneEntry t;
+        if (tune_lookup(p, &t)) {  // this shape was tuned before in this process
+            for (int i = 0; i < 5; ++i) p->var[i] = t.var[i];
+            if ((t.mode == 1 || t.mode == 2) && (e = fused_prepare(p, st)) != cudaSuccess) {
+                free_plan(p);
+                return cuda_status(e);
+            }
+            p->use_fused = t.mode;
+        } else {
+            poisson_status s = autotune(p, st);
+            if (s != POISSON_OK) { free_plan(p); return s; }
+            tune_store(p);
+        }
     }
     *out = p;
     return POISSON_OK;
@@ -611,7 +662,9 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
 
 poisson_status poisson_plan_autotune(poisson_plan_t plan, void* cuda_stream) {
     if (!plan) return POISSON_ERR_ARG;
-    return autotune(plan, static_cast<cudaStream_t>(cuda_stream));
+    const poisson_status s = autotune(plan, static_cast<cudaStream_t>(cuda_stream));
+    if (s == POISSON_OK) tune_store(plan);
+    return s;
 }
 
 poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int variant) {
@@ -700,7 +753,7 @@ poisson_status poisson_batch_get_mode(poisson_plan_t const* plans, int count, in
 }
 
 poisson_status poisson_batch_set_mode(poisson_plan_t const* plans, int count, int mode) {
-    if (!plans || count <= 0 || mode < -1 || mode > 1) return POISSON_ERR_ARG;
+    if (!plans || count <= 0 || mode < -1 || mode > 2) return POISSON_ERR_ARG;
     return pgb::batch_mode(plans, count, mode, nullptr);
 }
 

@@ -3,10 +3,13 @@
 // caller's data and keeps the faster; POISSON_BATCH_MODE=0/1 forces one):
 //
 //  mode 0: ONE persistent kernel over the tiles of all fields (below);
-//  mode 1: every field's own five (autotuned) kernels, captured once into a
-//          graph whose branches spread the fields over four streams
-//          (largest fields first, each to the least loaded stream), so small
-//          fields run side by side.
+//  mode 1: every field's own five kernels (each plan's own, possibly
+//          autotuned, variants), captured once into a graph whose branches
+//          spread the fields over four streams (largest fields first, each
+//          to the least loaded stream), so small fields run side by side;
+//  mode 2: the same graph with the variants plans use untuned: variants
+//          tuned for a field alone on the GPU are not always the best ones
+//          when fields share it.
 //
 // Work items are tiles of the five passes of every field.  The queue is laid
 // out pass-major (all x-forward tiles, then all y-forward tiles, ...) with
@@ -218,12 +221,12 @@ constexpr int BATCH_STREAMS = 4;
 struct BatchState {
     std::vector<poisson_plan_t> plans;
     int hold_field = -1;
-    int mode = -1;                   // 0 persistent kernel, 1 per-field launches, -1 undecided
+    int mode = -1;                   // 0 persistent kernel, 1/2 per-field launches, -1 undecided
     cudaStream_t side[BATCH_STREAMS] = {};
     cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
-    cudaGraphExec_t lexec = nullptr;  // mode-1 graph, for the pointers in lrho/lphi
-    std::vector<const void*> lrho;
-    std::vector<void*> lphi;
+    cudaGraphExec_t lexec[2] = {};   // mode 1 and mode 2 graphs, for the pointers in lrho/lphi
+    std::vector<const void*> lrho[2];
+    std::vector<void*> lphi[2];
     int device = 0;
     BatchField* h_fields = nullptr;  // pinned mirror of d_fields
     BatchField* d_fields = nullptr;
@@ -241,7 +244,8 @@ std::vector<BatchState*> g_cache;
 
 void destroy_state(BatchState* b) {
     if (!b) return;
-    if (b->lexec) cudaGraphExecDestroy(b->lexec);
+    for (int k = 0; k < 2; ++k)
+        if (b->lexec[k]) cudaGraphExecDestroy(b->lexec[k]);
     for (int k = 0; k < BATCH_STREAMS; ++k) {
         if (b->side[k]) cudaStreamDestroy(b->side[k]);
         if (b->join[k]) cudaEventDestroy(b->join[k]);
@@ -368,7 +372,8 @@ bool same_plans(const BatchState* b, poisson_plan_t const* plans, int count, int
 
 // Queue every field's five kernels, spread over the side streams (forked
 // from and joined back to `st`); usable eagerly or under stream capture.
-cudaError_t enqueue_fields(BatchState* b, const void* const* rho, void* const* phi, cudaStream_t st) {
+cudaError_t enqueue_fields(BatchState* b, const void* const* rho, void* const* phi, cudaStream_t st,
+                           bool defaults) {
     cudaError_t e;
     const int n = (int)b->plans.size();
     if (!b->fork) {
@@ -394,8 +399,10 @@ cudaError_t enqueue_fields(BatchState* b, const void* const* rho, void* const* p
         for (int j = 1; j < BATCH_STREAMS; ++j)
             if (load[j] < load[k]) k = j;
         load[k] += cells(i);
-        for (int pass = 0; pass < 5; ++pass)
-            if ((e = plan_run_pass(b->plans[i], pass, rho[i], phi[i], b->side[k]))) return e;
+        for (int pass = 0; pass < 5; ++pass) {
+            const int var = defaults ? plan_default_variant(b->plans[i], pass) : -1;
+            if ((e = plan_run_pass(b->plans[i], pass, rho[i], phi[i], b->side[k], var))) return e;
+        }
     }
     for (int k = 0; k < BATCH_STREAMS; ++k) {
         if ((e = cudaEventRecord(b->join[k], b->side[k]))) return e;
@@ -405,30 +412,31 @@ cudaError_t enqueue_fields(BatchState* b, const void* const* rho, void* const* p
 }
 
 // (Re)build the mode-1 graph for these buffers.
-cudaError_t build_launch_graph(BatchState* b, const void* const* rho, void* const* phi) {
+cudaError_t build_launch_graph(BatchState* b, const void* const* rho, void* const* phi, int mode) {
     cudaError_t e;
-    if (b->lexec) {
-        cudaGraphExecDestroy(b->lexec);
-        b->lexec = nullptr;
+    const int k = mode - 1;
+    if (b->lexec[k]) {
+        cudaGraphExecDestroy(b->lexec[k]);
+        b->lexec[k] = nullptr;
     }
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) return e;
     // warm the kernels (attributes, module loading) outside the capture
-    e = enqueue_fields(b, rho, phi, cs);
+    e = enqueue_fields(b, rho, phi, cs, mode == 2);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     cudaGraph_t g = nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t e2 = enqueue_fields(b, rho, phi, cs);
+        cudaError_t e2 = enqueue_fields(b, rho, phi, cs, mode == 2);
         e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->lexec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->lexec[k], g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     const int n = (int)b->plans.size();
-    b->lrho.assign(rho, rho + n);
-    b->lphi.assign(phi, phi + n);
+    b->lrho[k].assign(rho, rho + n);
+    b->lphi[k].assign(phi, phi + n);
     return e;
 }
 
@@ -501,30 +509,31 @@ poisson_status batched_solve(poisson_plan_t const* plans, int count, const void*
         if ((e = cudaEventRecord(b->copied, st))) return POISSON_ERR_CUDA;
         b->have_ptrs = true;
     }
-    // mode 1 needs a graph captured for exactly these buffers
-    auto launch_mode1 = [&]() -> cudaError_t {
-        bool same = b->lexec != nullptr;
-        for (int i = 0; i < count && same; ++i) same = b->lrho[i] == rho[i] && b->lphi[i] == phi[i];
-        if (!same && (e = build_launch_graph(b, rho, phi))) return e;
-        return cudaGraphLaunch(b->lexec, st);
+    // modes 1 and 2 need a graph captured for exactly these buffers
+    auto launch = [&](int m) -> cudaError_t {
+        if (m == 0) return cudaGraphLaunch(b->exec, st);
+        const int k = m - 1;
+        bool same = b->lexec[k] != nullptr;
+        for (int i = 0; i < count && same; ++i) same = b->lrho[k][i] == rho[i] && b->lphi[k][i] == phi[i];
+        if (!same && (e = build_launch_graph(b, rho, phi, m))) return e;
+        return cudaGraphLaunch(b->lexec[k], st);
     };
     if (b->mode < 0) {
         const char* forced = std::getenv("POISSON_BATCH_MODE");
         if (hold >= 0) {
             b->mode = 0;
-        } else if (forced && (forced[0] == '0' || forced[0] == '1')) {
+        } else if (forced && forced[0] >= '0' && forced[0] <= '2') {
             b->mode = forced[0] - '0';
         } else {
-            // time both executions on the caller's data (twice each, keep the
-            // second) and keep the faster
+            // time the three executions on the caller's data (twice each,
+            // keep the second) and keep the fastest
             cudaEvent_t t0, t1;
             if ((e = cudaEventCreate(&t0)) || (e = cudaEventCreate(&t1))) return POISSON_ERR_CUDA;
-            float ms[2] = {0.f, 0.f};
-            for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+            float ms[3] = {0.f, 0.f, 0.f};
+            for (int m = 0; m < 3 && e == cudaSuccess; ++m)
                 for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                     if ((e = cudaEventRecord(t0, st))) break;
-                    e = m == 0 ? cudaGraphLaunch(b->exec, st) : launch_mode1();
-                    if (e) break;
+                    if ((e = launch(m))) break;
                     if ((e = cudaEventRecord(t1, st))) break;
                     if ((e = cudaEventSynchronize(t1))) break;
                     e = cudaEventElapsedTime(&ms[m], t0, t1);
@@ -532,11 +541,14 @@ poisson_status batched_solve(poisson_plan_t const* plans, int count, const void*
             cudaEventDestroy(t0);
             cudaEventDestroy(t1);
             if (e != cudaSuccess) return POISSON_ERR_CUDA;
-            b->mode = ms[1] < ms[0] ? 1 : 0;
+            int best = 0;
+            for (int m = 1; m < 3; ++m)
+                if (ms[m] < ms[best]) best = m;
+            b->mode = best;
             return POISSON_OK;  // the timing runs already produced the result
         }
     }
-    e = b->mode == 0 ? cudaGraphLaunch(b->exec, st) : launch_mode1();
+    e = launch(b->mode);
     return e == cudaSuccess ? POISSON_OK : POISSON_ERR_CUDA;
 }
 

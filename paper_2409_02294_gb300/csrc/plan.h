@@ -41,7 +41,11 @@ namespace pgb {
 // the plan is destroyed).
 void batch_forget_plan(poisson_plan_t plan);
 // One pass (0..4) of the five-launch solve with the plan's kernel variants.
-cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st);
+// One pass of a plan's solve, with the plan's variant (var < 0) or var.
+cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, void* phi, cudaStream_t st,
+                          int var = -1);
+// The variant a plan uses for a pass when it is not autotuned.
+int plan_default_variant(const poisson_plan_s* pl, int pass);
 // Single-field fused dataflow solve (fused.cu).
 template <class R> struct PassParams;
 bool fused_supported(const poisson_plan_s* pl);

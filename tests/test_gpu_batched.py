@@ -30,7 +30,7 @@ def _rel(a, b):
     return (np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max())
 
 
-@pytest.mark.parametrize("mode", ["0", "1", "auto"])
+@pytest.mark.parametrize("mode", ["0", "1", "2", "auto"])
 def test_batched_matches_single_solves_and_oracle(pg, oracle_mod, mode, monkeypatch):
     if mode == "auto":
         monkeypatch.delenv("POISSON_BATCH_MODE", raising=False)
@@ -46,7 +46,7 @@ def test_batched_matches_single_solves_and_oracle(pg, oracle_mod, mode, monkeypa
             torch.cuda.synchronize()
             assert plans[0].sync_status() == 0
             chosen = pg.batch_mode(plans)
-            assert chosen in (0, 1) and (mode == "auto" or chosen == int(mode))
+            assert chosen in (0, 1, 2) and (mode == "auto" or chosen == int(mode))
             for i, (p, r, o) in enumerate(zip(plans, rhos, phis)):
                 ref = p.solve(r)
                 l2, mx = _rel(o, ref)
@@ -64,27 +64,30 @@ def test_batch_mode_switch_keeps_results(pg, monkeypatch):
     monkeypatch.delenv("POISSON_BATCH_MODE", raising=False)
     shapes = SHAPES[:4]
     plans = [pg.Plan(s[2], s[1], s[0]) for s in shapes]
+    for p in plans:  # non-default variants, so that modes 1 and 2 run different kernels
+        for ps, v in ((0, 1), (1, 4), (2, 0), (3, 2), (4, 0)):
+            p.set_variant(ps, v)
     try:
         with pytest.raises(pg.PoissonError):
             pg.batch_mode(plans, 0)  # no cached batch for this plan list yet
         assert pg.batch_mode(plans) == -1
         rhos = [torch.randn(s, device="cuda") for s in shapes]
         outs = []
-        for m in (0, 1):
+        first = [torch.empty_like(r) for r in rhos]
+        pg.solve_batched(plans, rhos, first)  # picks a mode by timing
+        torch.cuda.synchronize()
+        assert plans[0].sync_status() == 0
+        for m in (0, 1, 2):
             phis = [torch.empty_like(r) for r in rhos]
-            if m == 1:
-                pg.batch_mode(plans, 1)
+            pg.batch_mode(plans, m)
             pg.solve_batched(plans, rhos, phis)
             torch.cuda.synchronize()
             assert plans[0].sync_status() == 0
-            if m == 0:
-                pg.batch_mode(plans, 0)
-                pg.solve_batched(plans, rhos, phis)
-                torch.cuda.synchronize()
             assert pg.batch_mode(plans) == m
             outs.append(phis)
-        for a, b in zip(*outs):
-            assert _rel(a, b)[0] <= 1e-6
+        for other in outs[1:]:
+            for a, b in zip(outs[0], other):
+                assert _rel(a, b)[0] <= 1e-6
     finally:
         for p in plans:
             p.close()

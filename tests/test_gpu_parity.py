@@ -403,3 +403,22 @@ def test_check_finite_flag_reports_non_finite_output(pg, precision):
     with pg.Plan(48, 32, 32, precision=precision) as plan:  # without the flag nothing is checked
         plan.solve(rho)
         assert plan.sync_status() == 0
+
+
+def test_autotune_result_is_reused_for_the_same_shape(pg, oracle_mod):
+    import time
+    shape = (32, 48, 96)
+    rho = np.random.default_rng(21).standard_normal(shape).astype(np.float32)
+    ref = oracle_mod.solve_fft(rho.astype(np.float64))
+    t0 = time.perf_counter()
+    with pg.Plan(96, 48, 32, flags=pg.abi.FLAG_AUTOTUNE) as a:
+        t_first = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        with pg.Plan(96, 48, 32, flags=pg.abi.FLAG_AUTOTUNE) as b:
+            t_second = time.perf_counter() - t0
+            ia, ib = a.info(), b.info()
+            assert ia["variant"] == ib["variant"] and ia["fused"] == ib["fused"]
+            out = b.solve(torch.from_numpy(rho).cuda()).double().cpu().numpy()
+    assert t_second < t_first  # the second plan took the recorded result
+    l2, mx = rel_errors(out, ref)
+    assert l2 <= TOL32[0] and mx <= TOL32[1]
