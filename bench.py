@@ -79,12 +79,18 @@ def pass_bytes(nx, ny, nz, rsize=4):  # rsize: bytes per real value
     return [cells * rsize + w1, w1 + w2, 2 * w2 + g, w2 + w1, w1 + cells * rsize]
 
 
+# the sources the pass kernels (five passes, tensor-core z pass) are built
+# from: a profile's counters stay valid while these are unchanged
+KERNEL_SOURCES = ("fft_core.cuh", "passes.cuh", "configs.cuh", "tma.cuh", "tc_dft.cuh", "internal.h",
+                  "twiddles.cu", "passes_f32_row.cu", "passes_f32_y.cu", "passes_f32_z.cu", "passes_f64.cu",
+                  "passes_tc.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_02294_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
