@@ -34,18 +34,22 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// One poll: suspends for at most kMbarPollNs (the explicit time hint bounds
+// each poll, so max_polls bounds the whole wait in time as well).
+constexpr unsigned kMbarPollNs = 1000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kMbarPollNs)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for phase `parity` of bar to complete.
+// Bounded wait for phase `parity` of bar to complete (at most about
+// max_polls microseconds).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int max_polls) {
     for (int i = 0; i < max_polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
