@@ -20,6 +20,8 @@
 //                       Green's function, scaled by -G V / (Mx My Mz)
 #pragma once
 
+#include <cstdlib>
+
 #include "fft_core.cuh"
 #include "tma.cuh"
 
@@ -789,7 +791,7 @@ constexpr int kTmaWaitPolls = 1 << 20;  // bounded wait for one tile's copy
 
 template <int PASS, class Cfg, int SLOTS, int LPT, int MINB>
 __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
-    k_col_tma(PassParams<float> p, const __grid_constant__ CUtensorMap map, int t0, int t1) {
+    k_col_tma(PassParams<float> p, const __grid_constant__ CUtensorMap map, int t0, int t1, int hold) {
     using B = TmaBox<PASS, Cfg, SLOTS>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* buf = reinterpret_cast<cpx<float>*>(smem_raw);  // buffer k at buf + k * ROWS * SLOTS
@@ -818,7 +820,7 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
     if (tile >= t1) return;
     const int G = (int)gridDim.x;
     if (threadIdx.x == 0) {
-        issue(tile, 0);
+        if (!hold) issue(tile, 0);  // test hook: the first copy is never issued, its wait runs out
         if (tile + G < t1) issue(tile + G, 1);
     }
     const int slot = threadIdx.x % SLOTS;
@@ -965,7 +967,10 @@ cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, i
         if ((e = tma_encode_3d_f32(&map, base, dims, strides, box)) != cudaSuccess) return e;
         const int count = w1 - t_begin;
         const int grid = count < per_sm[d] ? count : per_sm[d];
-        kern<<<grid, NT, sm, st>>>(p, map, t_begin, w1);
+        // test hook (failure detection without a GPU fault): the first copy of
+        // every CTA is skipped, so its bounded wait runs out and reports
+        const char* hold = std::getenv("POISSON_TEST_TMA_HOLD");
+        kern<<<grid, NT, sm, st>>>(p, map, t_begin, w1, hold && hold[0] == '1' ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int n0 = t_begin > n_wide ? t_begin : n_wide;

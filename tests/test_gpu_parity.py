@@ -422,3 +422,23 @@ def test_autotune_result_is_reused_for_the_same_shape(pg, oracle_mod):
     assert t_second < t_first  # the second plan took the recorded result
     l2, mx = rel_errors(out, ref)
     assert l2 <= TOL32[0] and mx <= TOL32[1]
+
+
+def test_tma_column_kernel_wait_timeout_is_reported(pg, oracle_mod, monkeypatch):
+    # Test hook: the persistent TMA kernel skips its first copy, so the bounded
+    # mbarrier wait (about a second) runs out; the kernel records a timeout in
+    # the status word and returns, and the GPU stays usable.
+    shape = (32, 32, 32)
+    rho = np.random.default_rng(31).standard_normal(shape).astype(np.float32)
+    x = torch.from_numpy(rho).cuda()
+    with pg.Plan(32) as plan:
+        tma = plan.info()["variant_count"][2] - 2  # first persistent TMA column variant
+        plan.set_variant(2, tma)
+        monkeypatch.setenv("POISSON_TEST_TMA_HOLD", "1")
+        plan.solve(x)
+        assert plan.sync_status() == 5  # POISSON_ERR_TIMEOUT
+        monkeypatch.delenv("POISSON_TEST_TMA_HOLD")
+        out = plan.solve(x).double().cpu().numpy()
+        assert plan.sync_status() == 0
+    ref = oracle_mod.solve_fft(rho.astype(np.float64))
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-6
