@@ -137,7 +137,9 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, voi
 /*
  * Solve `count` independent fields, plans[i] applied to rho_dev[i] ->
  * phi_dev[i].  Plans may have different sizes but must share the device
- * and precision (FP32).  Three executions exist, each replayed from a CUDA
+ * and precision (FP32); each plan appears at most once (a plan owns one
+ * workspace and the fields run at the same time: use one plan per field, or
+ * poisson_solve_host_levels, which serialises repeats).  Three executions exist, each replayed from a CUDA
  * graph: (0) one persistent kernel over the tiles of all fields, with
  * bounded per-field dependency waits; (1) every field's own five kernels
  * with each plan's own (possibly autotuned) variants, captured into one
@@ -148,7 +150,8 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, voi
  * (synchronising cuda_stream) and keeps the fastest; the environment
  * variable POISSON_BATCH_MODE=0, 1 or 2 forces one.  Later calls replay the
  * chosen graph (modes 1 and 2 re-capture when the buffers change).  The arrays of
- * pointers are host arrays.  Errors: POISSON_ERR_ARG, POISSON_ERR_UNSUPPORTED
+ * pointers are host arrays.  Errors: POISSON_ERR_ARG (also for a repeated
+ * plan), POISSON_ERR_UNSUPPORTED
  * (mixed precision or devices), POISSON_ERR_CUDA, POISSON_ERR_TIMEOUT
  * (reported by poisson_plan_sync_status on plans[0]).
  */

@@ -343,18 +343,30 @@ def batch_mode(plans, mode=None):
 def _make_autograd():
     torch = _torch()
 
+    def each(fn, x):
+        # one field [nz, ny, nx], or a leading batch dimension solved field by
+        # field on the current stream (one plan, so the solves run in order)
+        x = x.contiguous()
+        if x.dim() == 3:
+            return fn(x)
+        out = torch.empty_like(x)
+        for b in range(x.shape[0]):
+            fn(x[b], out=out[b])
+        return out
+
     class PoissonSolve(torch.autograd.Function):
-        """Phi = solve(rho); the backward pass is the hand-written adjoint
-        (correlation with the Green's function) of libpoisson."""
+        """Phi = solve(rho) for rho of shape [nz, ny, nx] or [B, nz, ny, nx];
+        the backward pass is the hand-written adjoint (correlation with the
+        Green's function) of libpoisson."""
 
         @staticmethod
         def forward(ctx, rho, plan):
             ctx.plan = plan
-            return plan.solve(rho.contiguous())
+            return each(plan.solve, rho)
 
         @staticmethod
         def backward(ctx, grad_phi):
-            return ctx.plan.adjoint(grad_phi.contiguous()), None
+            return each(ctx.plan.adjoint, grad_phi), None
 
     return PoissonSolve
 

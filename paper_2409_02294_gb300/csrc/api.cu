@@ -1,4 +1,5 @@
 // C-ABI of libpoisson (declared in include/poisson.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -764,6 +765,11 @@ poisson_status poisson_solve_batched(poisson_plan_t const* plans, int count, con
         poisson_status s = check_io(plans[i], rho_dev[i], phi_dev[i]);
         if (s != POISSON_OK) return s;
     }
+    // each plan at most once: a plan owns one workspace, and the fields of a
+    // batch run at the same time
+    std::vector<poisson_plan_t> sorted(plans, plans + count);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return POISSON_ERR_ARG;
     return pgb::batched_solve(plans, count, rho_dev, phi_dev, static_cast<cudaStream_t>(cuda_stream));
 }
 

@@ -93,12 +93,14 @@ def test_batch_mode_switch_keeps_results(pg, monkeypatch):
             p.close()
 
 
-def test_batched_rejects_mixed_precision_and_empty(pg):
+def test_batched_rejects_mixed_precision_repeated_plans_and_empty(pg):
     with pg.Plan(32) as a, pg.Plan(32, precision="fp64") as b:
         x = torch.zeros((32, 32, 32), device="cuda")
         y = torch.zeros((32, 32, 32), device="cuda", dtype=torch.float64)
         with pytest.raises(pg.PoissonError):
             pg.solve_batched([a, b], [x, y], [torch.empty_like(x), torch.empty_like(y)])
+        with pytest.raises(pg.PoissonError):  # one workspace per plan: no repeats
+            pg.solve_batched([a, a], [x, x.clone()], [torch.empty_like(x), torch.empty_like(x)])
     pg.solve_batched([], [], [])
 
 

@@ -442,3 +442,15 @@ def test_tma_column_kernel_wait_timeout_is_reported(pg, oracle_mod, monkeypatch)
         assert plan.sync_status() == 0
     ref = oracle_mod.solve_fft(rho.astype(np.float64))
     assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+def test_autograd_with_a_batch_dimension(pg):
+    rng = np.random.default_rng(41)
+    rho = torch.from_numpy(rng.standard_normal((3, 16, 32, 48)).astype(np.float32)).cuda().requires_grad_()
+    w = torch.from_numpy(rng.standard_normal((3, 16, 32, 48)).astype(np.float32)).cuda()
+    with pg.Plan(48, 32, 16) as plan:
+        phi = pg.PoissonSolve.apply(rho, plan)
+        (w * phi).sum().backward()
+        for b in range(3):
+            assert torch.equal(phi[b], plan.solve(rho[b].detach().contiguous()))
+            assert torch.equal(rho.grad[b], plan.adjoint(w[b].contiguous()))
