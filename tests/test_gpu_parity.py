@@ -454,3 +454,19 @@ def test_autograd_with_a_batch_dimension(pg):
         for b in range(3):
             assert torch.equal(phi[b], plan.solve(rho[b].detach().contiguous()))
             assert torch.equal(rho.grad[b], plan.adjoint(w[b].contiguous()))
+
+
+def test_fp64_solve_matches_the_golden_fixture(pg):
+    # the stored direct pair sums (tests/golden, written by the oracle)
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("make_golden", path)
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    data = np.loadtxt(mg.OUT, comments="#")
+    idx, want = data[:, 0].astype(np.int64), data[:, 4]
+    nz, ny, nx = mg.SHAPE
+    with pg.Plan(nx, ny, nz, h=mg.H, precision="fp64") as plan:
+        out = plan.solve(torch.from_numpy(mg.density()).cuda()).cpu().numpy().ravel()
+    assert np.abs(out[idx] - want).max() <= 1e-11 * np.abs(want).max()

@@ -405,3 +405,24 @@ def test_user_kernel_with_the_greens_octant_is_the_poisson_solve(oracle_mod):
     a = oracle_mod.solve_direct_kernel(rho, koct, -1.0 * 1.0 * 0.5 * 2.0)
     b = oracle_mod.solve_direct(rho, h=h)
     assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+
+
+# ---------------------------------------------------------------------------
+# golden fixture (tests/golden): written by the oracle; pins it against change
+# ---------------------------------------------------------------------------
+
+def _golden():
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("make_golden", path)
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    data = np.loadtxt(mg.OUT, comments="#")
+    return mg, data[:, 0].astype(np.int64), data[:, 4]
+
+
+def test_oracle_reproduces_the_golden_fixture(oracle_mod):
+    mg, idx, phi = _golden()
+    got = oracle_mod.sample_direct(mg.density(), idx, h=mg.H, G=1.0)
+    assert np.abs(got - phi).max() <= 1e-13 * np.abs(phi).max()
