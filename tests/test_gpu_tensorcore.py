@@ -77,3 +77,20 @@ def test_adjoint_directional_fd_on_subblock(pg, prec):
         an = float((g.double() * v.double()).sum())
     tol = {"fp32": 1e-5, "tc_fp16x2": 1e-5, "tc_bf16x2": 2e-4}[prec]
     assert fd == pytest.approx(an, rel=tol)
+
+
+@pytest.mark.parametrize("prec", ["tc_fp16x2", "tc_bf16x2"])
+def test_tensor_core_384cube_plummer_sampled(pg, oracle_mod, prec):
+    # one field of the 8 x 384^3 tensor-core workload at full size, autotuned
+    # as in the benchmark, against direct pair sums at sampled cells
+    rho, _ = workloads.plummer_spheres(384, count=16, seed=2409)
+    rho32 = rho.astype(np.float32)
+    with pg.Plan(384, precision=prec, flags=pg.abi.FLAG_AUTOTUNE) as plan:
+        out = plan.solve(torch.from_numpy(rho32).cuda()).double().cpu().numpy().reshape(-1)
+    n = 384
+    rng = np.random.default_rng(19)
+    idx = np.concatenate([rng.choice(n ** 3, 20, replace=False),
+                          np.array([0, n ** 3 - 1, (n // 2) * n * n + (n // 2) * n + n // 2])])
+    ref = oracle_mod.sample_direct(rho32.astype(np.float64), idx)
+    err = np.abs(out[idx] - ref).max() / np.abs(ref).max()
+    assert err <= TOL[prec][1], (prec, err)
