@@ -470,3 +470,42 @@ def test_fp64_solve_matches_the_golden_fixture(pg):
     with pg.Plan(nx, ny, nz, h=mg.H, precision="fp64") as plan:
         out = plan.solve(torch.from_numpy(mg.density()).cuda()).cpu().numpy().ravel()
     assert np.abs(out[idx] - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def _prism_potential(x, y, z, a, b, c):
+    """Integral of 1/|p - r| over the box [0,a] x [0,b] x [0,c] at points
+    p = (x, y, z) (the potential of a homogeneous rectangular prism of unit
+    density: the 8-corner sum of the classical antiderivative)."""
+    def F(u, v, w):
+        r = np.sqrt(u * u + v * v + w * w)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = (v * w * np.log(u + r) + w * u * np.log(v + r) + u * v * np.log(w + r)
+                 - 0.5 * u * u * np.arctan(v * w / (u * r)) - 0.5 * v * v * np.arctan(w * u / (v * r))
+                 - 0.5 * w * w * np.arctan(u * v / (w * r)))
+        return t
+    # upper limits (a - x, ...) with sign +, lower limits (-x, ...) with sign -
+    tot = 0.0
+    for i, u in ((0, a - x), (1, -x)):
+        for j, v in ((0, b - y), (1, -y)):
+            for k, w in ((0, c - z), (1, -z)):
+                tot = tot + (-1) ** (i + j + k) * F(u, v, w)
+    return tot
+
+
+@pytest.mark.parametrize("shape,h", [((32, 32, 32), (1.0, 1.0, 1.0)), ((32, 48, 64), (1.0, 0.75, 0.5))])
+def test_uniform_density_over_the_whole_grid_is_the_prism_potential(pg, shape, h):
+    # r_near >= n: every cell pair uses the exact cell average, so Phi at a
+    # cell centre is -G rho0 times the integral of 1/r over the whole box
+    nz, ny, nx = shape
+    rho0, G = 1.5, 0.8
+    rho = np.full(shape, rho0, dtype=np.float32)
+    with pg.Plan(nx, ny, nz, h=h, G=G, r_near=max(shape)) as plan:
+        out = plan.solve(torch.from_numpy(rho).cuda()).double().cpu().numpy()
+    rng = np.random.default_rng(5)
+    pts = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz // 2, ny // 2, nx // 2)] + \
+        [tuple(int(rng.integers(0, s)) for s in shape) for _ in range(20)]
+    hx, hy, hz = h
+    for iz, iy, ix in pts:
+        want = -G * rho0 * _prism_potential((ix + 0.5) * hx, (iy + 0.5) * hy, (iz + 0.5) * hz,
+                                            nx * hx, ny * hy, nz * hz)
+        assert abs(out[iz, iy, ix] - want) <= 2e-6 * abs(want), ((iz, iy, ix), out[iz, iy, ix], want)

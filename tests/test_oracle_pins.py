@@ -426,3 +426,40 @@ def test_oracle_reproduces_the_golden_fixture(oracle_mod):
     mg, idx, phi = _golden()
     got = oracle_mod.sample_direct(mg.density(), idx, h=mg.H, G=1.0)
     assert np.abs(got - phi).max() <= 1e-13 * np.abs(phi).max()
+
+
+def test_cell_averages_add_up_to_the_whole_box_integral(oracle_mod):
+    # with r_near >= n every pair uses the exact cell average, so the direct
+    # sum for a uniform density is the potential of the whole box: the
+    # classical prism antiderivative over its 8 corners, written out here
+    # independently and anchored by the textbook cube-centre value
+    def F(u, v, w):
+        r = math.sqrt(u * u + v * v + w * w)
+        t = 0.0
+        if r > 0:
+            t += v * w * math.log(u + r) if u + r > 0 else 0.0
+            t += w * u * math.log(v + r) if v + r > 0 else 0.0
+            t += u * v * math.log(w + r) if w + r > 0 else 0.0
+            if u != 0:
+                t -= 0.5 * u * u * math.atan(v * w / (u * r))
+            if v != 0:
+                t -= 0.5 * v * v * math.atan(w * u / (v * r))
+            if w != 0:
+                t -= 0.5 * w * w * math.atan(u * v / (w * r))
+        return t
+
+    def box(x, y, z, a, b, c):
+        tot = 0.0
+        for i, u in ((0, a - x), (1, -x)):
+            for j, v in ((0, b - y), (1, -y)):
+                for k, w in ((0, c - z), (1, -z)):
+                    tot += (-1) ** (i + j + k) * F(u, v, w)
+        return tot
+
+    s3 = math.sqrt(3.0)
+    assert box(0.5, 0.5, 0.5, 1, 1, 1) == pytest.approx(3 * math.log((s3 + 1) / (s3 - 1)) - math.pi / 2, rel=1e-14)
+    n, h = (16, 8, 12), (1.0, 0.75, 0.5)
+    phi = oracle_mod.solve_direct(np.ones(n), h=h, G=1.0, r_near=16)
+    for iz, iy, ix in [(0, 0, 0), (8, 4, 6), (15, 7, 11), (3, 5, 2), (10, 0, 9)]:
+        want = -box((ix + 0.5) * h[0], (iy + 0.5) * h[1], (iz + 0.5) * h[2], n[2] * h[0], n[1] * h[1], n[0] * h[2])
+        assert phi[iz, iy, ix] == pytest.approx(want, rel=1e-12)
