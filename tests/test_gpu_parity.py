@@ -509,3 +509,29 @@ def test_uniform_density_over_the_whole_grid_is_the_prism_potential(pg, shape, h
         want = -G * rho0 * _prism_potential((ix + 0.5) * hx, (iy + 0.5) * hy, (iz + 0.5) * hz,
                                             nx * hx, ny * hy, nz * hz)
         assert abs(out[iz, iy, ix] - want) <= 2e-6 * abs(want), ((iz, iy, ix), out[iz, iy, ix], want)
+
+
+def test_reflection_and_translation_at_size(pg):
+    # the kernel is even: flipping rho along an axis flips Phi; the
+    # free-space convolution is translation covariant: shifting a density
+    # whose support stays inside the grid shifts Phi on the overlap
+    shape = (64, 96, 128)
+    nz, ny, nx = shape
+    rho = np.zeros(shape, dtype=np.float32)
+    inner, _ = workloads.gaussian_blobs((32, 48, 64), count=5, seed=23)
+    rho[16:48, 24:72, 32:96] = inner.astype(np.float32)
+    s = (3, -5, 7)
+    shifted = np.roll(rho, s, axis=(0, 1, 2))  # support stays inside: nothing wraps
+    with pg.Plan(nx, ny, nz) as plan:
+        def solve(a):
+            return plan.solve(torch.from_numpy(np.ascontiguousarray(a)).cuda()).double().cpu().numpy()
+        base = solve(rho)
+        scale = np.abs(base).max()
+        for ax in range(3):
+            assert np.abs(solve(np.flip(rho, ax)) - np.flip(base, ax)).max() <= 2e-6 * scale
+        moved = solve(shifted)
+    z0, y0, x0 = max(s[0], 0), max(s[1], 0), max(s[2], 0)
+    z1, y1, x1 = nz + min(s[0], 0), ny + min(s[1], 0), nx + min(s[2], 0)
+    a = moved[z0:z1, y0:y1, x0:x1]
+    b = base[z0 - s[0]:z1 - s[0], y0 - s[1]:y1 - s[1], x0 - s[2]:x1 - s[2]]
+    assert np.abs(a - b).max() <= 2e-6 * scale
