@@ -588,10 +588,8 @@ poisson_status poisson_solve_host_levels(poisson_plan_t const* plans, int count,
             if (plans[j] == pl && ++seen == 2) prev = j;
         void** sin = (occ & 1) ? &pl->stage_in2 : &pl->stage_in;
         void** sout = (occ & 1) ? &pl->stage_out2 : &pl->stage_out;
-        if (!*sin) {
-            if ((e = cudaMalloc(sin, bytes))) return cuda_status(e);
-            if ((e = cudaMalloc(sout, bytes))) return cuda_status(e);
-        }
+        if (!*sin && (e = cudaMalloc(sin, bytes))) return cuda_status(e);
+        if (!*sout && (e = cudaMalloc(sout, bytes))) return cuda_status(e);
         cudaEvent_t in_done = ev[3 * i], solved = ev[3 * i + 1], out_done = ev[3 * i + 2];
         // copy-in stream: level i's rho, once the earlier solve from this pair has read it
         if (prev >= 0 && (e = cudaStreamWaitEvent(hp.in, ev[3 * prev + 1], 0))) return cuda_status(e);
@@ -629,10 +627,9 @@ poisson_status poisson_solve_host(poisson_plan_t plan, const void* rho_host, voi
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t bytes = (size_t)plan->nx * plan->ny * plan->nz * plan->rsize;
     cudaError_t e;
-    if (!plan->stage_in) {
-        if ((e = cudaMalloc(&plan->stage_in, bytes)) != cudaSuccess) return cuda_status(e);
-        if ((e = cudaMalloc(&plan->stage_out, bytes)) != cudaSuccess) return cuda_status(e);
-    }
+    // each buffer on its own: a failed allocation leaves the other usable
+    if (!plan->stage_in && (e = cudaMalloc(&plan->stage_in, bytes)) != cudaSuccess) return cuda_status(e);
+    if (!plan->stage_out && (e = cudaMalloc(&plan->stage_out, bytes)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemcpyAsync(plan->stage_in, rho_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_status(e);
     poisson_status s = solve_all(plan, plan->stage_in, plan->stage_out, st);
