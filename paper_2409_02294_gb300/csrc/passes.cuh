@@ -313,7 +313,17 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
         const R* g = p.greens + (long long)kyf * (nx + 1) + c.kx;
         constexpr int TPS = (LPT == 1 ? 2 : 1) * T;  // threads per slot
         const int u = id.t + (LPT == 1 ? id.q * T : 0);
-        for (int kz = u; kz <= N; kz += TPS) cp_async_real(gsl + gsl_idx<R, SLOTS>(kz, id.slot), g + kz * gz);
+        if constexpr (TPS % gsl_group<R, SLOTS>() == 0) {
+            // rows u + TPS i keep u's place within their block of G rows, so
+            // the staged index and the source advance by constant steps
+            R* sp = gsl + gsl_idx<R, SLOTS>(u, id.slot);
+            const R* gp = g + u * gz;
+#pragma unroll
+            for (int i = 0; i < N / TPS; ++i) cp_async_real(sp + i * TPS * SLOTS, gp + i * TPS * gz);
+            if (u == 0) cp_async_real(sp + N * SLOTS, gp + N * gz);
+        } else {
+            for (int kz = u; kz <= N; kz += TPS) cp_async_real(gsl + gsl_idx<R, SLOTS>(kz, id.slot), g + kz * gz);
+        }
     }
     cp_async_commit();
 
@@ -344,11 +354,23 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
 #pragma unroll
         for (int l = 0; l < LPT; ++l) {
             const int kz0 = 2 * id.t + id.half(l);
+            if constexpr (T % gsl_group<R, SLOTS>() == 0) {
+                // kz0 + 2 T m and 2N - kz0 - 2 T m keep the place of kz0 and
+                // 2N - kz0 within their blocks of G rows: constant offsets
+                // from two bases (the second base, beyond row N for small
+                // kz0, is only read back at rows <= N)
+                const int i_lo = gsl_idx<R, SLOTS>(kz0, id.slot);
+                const int i_hi = gsl_idx<R, SLOTS>(2 * N - kz0, id.slot);
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int kz = kz0 + 2 * T * m;
-                const int kzf = (m < E / 2) ? kz : 2 * N - kz;
-                v[l][m] = scale(v[l][m], gsl[gsl_idx<R, SLOTS>(kzf, id.slot)]);
+                for (int m = 0; m < E; ++m)
+                    v[l][m] = scale(v[l][m], gsl[m < E / 2 ? i_lo + 2 * T * m * SLOTS : i_hi - 2 * T * m * SLOTS]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int kz = kz0 + 2 * T * m;
+                    const int kzf = (m < E / 2) ? kz : 2 * N - kz;
+                    v[l][m] = scale(v[l][m], gsl[gsl_idx<R, SLOTS>(kzf, id.slot)]);
+                }
             }
         }
     }
