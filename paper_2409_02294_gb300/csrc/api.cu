@@ -61,9 +61,10 @@ void host_twiddle(long long j, long long n, double* c, double* s) {
 }
 
 template <class R>
-cudaError_t upload_twiddles(int n, void** dst, cudaStream_t st) {
+cudaError_t upload_twiddles(int n, bool row, void** dst, cudaStream_t st) {
     // W_2n^j, j < 2n, then the per-stage tables gathered from it on the device
-    const int entries = axis_tw_list<R>(n).total;
+    // (the row passes' layout for the x axis, the column passes' for y and z)
+    const int entries = axis_tw_list<R>(n, row).total;
     std::vector<R> h(4 * (size_t)n);
     for (long long j = 0; j < 2 * n; ++j) {
         double c, s;
@@ -75,7 +76,7 @@ cudaError_t upload_twiddles(int n, void** dst, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(*dst, h.data(), h.size() * sizeof(R), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    e = fill_stage_twiddles<R>(static_cast<cpx<R>*>(*dst), n, st);
+    e = fill_stage_twiddles<R>(static_cast<cpx<R>*>(*dst), n, row, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);  // h goes out of scope
 }
@@ -471,8 +472,8 @@ poisson_status create_plan(poisson_plan_t* out, int nx, int ny, int nz, double h
     }
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a) {
-        e = prec == POISSON_FP64 ? upload_twiddles<double>(dims[a], &p->tw[a], st)
-                                 : upload_twiddles<float>(dims[a], &p->tw[a], st);
+        e = prec == POISSON_FP64 ? upload_twiddles<double>(dims[a], a == 0, &p->tw[a], st)
+                                 : upload_twiddles<float>(dims[a], a == 0, &p->tw[a], st);
         if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
     }
     // the inverse transform's 1/(Mx My Mz) is folded into Ghat

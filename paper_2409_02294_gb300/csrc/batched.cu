@@ -64,25 +64,27 @@ struct BatchArgs {
 };
 
 template <int N> struct BatchShape {
-    using C = typename SizeCfg<float, N>::C;
+    using C = typename SizeCfg<float, N>::C;      // column tiles
+    using RC = typename RowSizeCfg<float, N>::C;  // row tiles
     static constexpr int S = var_slots<C, BatchVar>();
-    static constexpr int P = var_pairs<C, BatchVar>();
+    static constexpr int P = var_pairs<RC, BatchVar>();
     static_assert(col_threads<C, S, 2>() == BATCH_THREADS, "column tile must use BATCH_THREADS threads");
-    static_assert(row_threads<C, P, 2>() == BATCH_THREADS, "row tile must use BATCH_THREADS threads");
-    static constexpr size_t smem = col_smem_z<C, S>() > row_smem<C, P>() ? col_smem_z<C, S>() : row_smem<C, P>();
+    static_assert(row_threads<RC, P, 2>() == BATCH_THREADS, "row tile must use BATCH_THREADS threads");
+    static constexpr size_t smem = col_smem_z<C, S>() > row_smem<RC, P>() ? col_smem_z<C, S>() : row_smem<RC, P>();
 };
 
 template <int N>
 __device__ __noinline__ void batch_tile(int pass, const PassParams<float>& p, int rows, int tile,
                                            unsigned char* sm) {
     using C = typename BatchShape<N>::C;
+    using RC = typename BatchShape<N>::RC;
     constexpr int S = BatchShape<N>::S, P = BatchShape<N>::P;
     switch (pass) {
-        case 0: tile_x_fwd<C, P, 2, true>(p, rows, tile, sm); break;
+        case 0: tile_x_fwd<RC, P, 2, true>(p, rows, tile, sm); break;
         case 1: tile_y_fwd<C, S, 2, true>(p, tile, sm); break;
         case 2: tile_z_conv<C, S, 2, true>(p, tile, sm); break;
         case 3: tile_y_inv<C, S, 2, true>(p, tile, sm); break;
-        default: tile_x_inv<C, P, 2, true>(p, rows, tile, sm); break;
+        default: tile_x_inv<RC, P, 2, true>(p, rows, tile, sm); break;
     }
 }
 

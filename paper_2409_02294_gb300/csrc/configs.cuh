@@ -42,27 +42,39 @@ inline bool size_supported(int n) {
     }
 }
 
-// Twiddle-table layout of an axis of edge n for the precision's radix
-// sequence (every kernel that transforms lines of n uses SizeCfg<R, n>).
-template <class R> inline StageTwList axis_tw_list(int n) {
+// The row passes (x axis) use RowSizeCfg: SizeCfg except where fewer values
+// per thread suit the row tiles (FP32 512: radices 16-16-2, 32 threads per
+// line; the column tiles keep 32-16, whose 16 threads per line give wider
+// column tiles).
+template <class R, int N> struct RowSizeCfg { using C = typename SizeCfg<R, N>::C; };
+template <> struct RowSizeCfg<float, 512> { using C = LineCfg<float, 512, 16, Radices<16, 16, 2>>; };
+
+// Twiddle-table layout of an axis of edge n: the row configuration's radix
+// sequence for the x axis (row = true), the column configuration's for y and
+// z (every kernel that transforms lines of an axis uses that configuration).
+template <class R, int N> inline StageTwList axis_tw_list_n(bool row) {
+    return row ? stage_tw_list<N>(typename RowSizeCfg<R, N>::C::Rads{})
+               : stage_tw_list<N>(typename SizeCfg<R, N>::C::Rads{});
+}
+template <class R> inline StageTwList axis_tw_list(int n, bool row) {
     switch (n) {
-        case 16: return stage_tw_list<16>(typename SizeCfg<R, 16>::C::Rads{});
-        case 32: return stage_tw_list<32>(typename SizeCfg<R, 32>::C::Rads{});
-        case 48: return stage_tw_list<48>(typename SizeCfg<R, 48>::C::Rads{});
-        case 64: return stage_tw_list<64>(typename SizeCfg<R, 64>::C::Rads{});
-        case 96: return stage_tw_list<96>(typename SizeCfg<R, 96>::C::Rads{});
-        case 128: return stage_tw_list<128>(typename SizeCfg<R, 128>::C::Rads{});
-        case 192: return stage_tw_list<192>(typename SizeCfg<R, 192>::C::Rads{});
-        case 256: return stage_tw_list<256>(typename SizeCfg<R, 256>::C::Rads{});
-        case 384: return stage_tw_list<384>(typename SizeCfg<R, 384>::C::Rads{});
-        case 512: return stage_tw_list<512>(typename SizeCfg<R, 512>::C::Rads{});
+        case 16: return axis_tw_list_n<R, 16>(row);
+        case 32: return axis_tw_list_n<R, 32>(row);
+        case 48: return axis_tw_list_n<R, 48>(row);
+        case 64: return axis_tw_list_n<R, 64>(row);
+        case 96: return axis_tw_list_n<R, 96>(row);
+        case 128: return axis_tw_list_n<R, 128>(row);
+        case 192: return axis_tw_list_n<R, 192>(row);
+        case 256: return axis_tw_list_n<R, 256>(row);
+        case 384: return axis_tw_list_n<R, 384>(row);
+        case 512: return axis_tw_list_n<R, 512>(row);
         default: return StageTwList{};
     }
 }
 
 // Fill the stage tables of an axis table whose first 2n entries (W_2n^j)
-// are already on the device (async on st).
-template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, cudaStream_t st);
+// are already on the device (async on st); row as for axis_tw_list.
+template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, bool row, cudaStream_t st);
 
 // Variants the autotuner chooses from (per pass and edge length).
 //   column passes (y forward, z convolve, y inverse): lines per thread and
@@ -134,10 +146,11 @@ template <class R> int col_slots_for(int N, int var) {
 // Dispatch one pass of group GROUP for edge length N (the pass's axis).
 template <class R, int GROUP, int N>
 cudaError_t launch_group_n(int pass, int var, const PassParams<R>& p, int rows, cudaStream_t st) {
-    using C = typename SizeCfg<R, N>::C;
     if constexpr (GROUP == GROUP_ROW) {
+        using C = typename RowSizeCfg<R, N>::C;
         return launch_row_var<C, typename Variants<R>::Row>(var, pass, p, rows, st);
     } else {
+        using C = typename SizeCfg<R, N>::C;
         return launch_col_var<C, typename Variants<R>::Col>(var, pass, p, st);
     }
 }

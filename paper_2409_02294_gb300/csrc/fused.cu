@@ -33,16 +33,17 @@ namespace pgb {
 constexpr int FUSED_THREADS = 128;
 
 template <int N> struct FusedShape {
-    using C = typename SizeCfg<float, N>::C;
+    using C = typename SizeCfg<float, N>::C;      // column tiles
+    using RC = typename RowSizeCfg<float, N>::C;  // row tiles
     static constexpr int L = C::E <= 16 ? 2 : 1;  // lines per thread
     using V = Var<L, FUSED_THREADS>;
     static constexpr int S = var_slots<C, V>();
-    static constexpr int P = var_pairs<C, V>();
+    static constexpr int P = var_pairs<RC, V>();
     static constexpr int XW = S < Seg<float>::XW ? S : Seg<float>::XW;
     static constexpr int NLW = S / XW;
     static_assert(col_threads<C, S, L>() == FUSED_THREADS, "column tile must use 128 threads");
-    static_assert(row_threads<C, P, L>() == FUSED_THREADS, "row tile must use 128 threads");
-    static constexpr size_t smem = col_smem_z<C, S>() > row_smem<C, P>() ? col_smem_z<C, S>() : row_smem<C, P>();
+    static_assert(row_threads<RC, P, L>() == FUSED_THREADS, "row tile must use 128 threads");
+    static constexpr size_t smem = col_smem_z<C, S>() > row_smem<RC, P>() ? col_smem_z<C, S>() : row_smem<RC, P>();
 };
 
 struct FusedArgs {
@@ -109,6 +110,7 @@ template <int N, int MINB>
 __global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused(FusedArgs a) {
     using F = FusedShape<N>;
     using C = typename F::C;
+    using RC = typename F::RC;
     constexpr int S = F::S, P = F::P, L = F::L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_ok;
@@ -149,11 +151,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused(FusedArgs a) {
         __syncthreads();
         if (!s_ok) return;
         switch (pass) {
-            case 0: tile_x_fwd<C, P, L, true>(a.p[0], a.rows, tile, smem_raw); break;
+            case 0: tile_x_fwd<RC, P, L, true>(a.p[0], a.rows, tile, smem_raw); break;
             case 1: tile_y_fwd<C, S, L, true>(a.p[1], tile, smem_raw); break;
             case 2: tile_z_conv<C, S, L, true>(a.p[2], tile, smem_raw); break;
             case 3: tile_y_inv<C, S, L, true>(a.p[3], tile, smem_raw); break;
-            default: tile_x_inv<C, P, L, true>(a.p[4], a.rows, tile, smem_raw); break;
+            default: tile_x_inv<RC, P, L, true>(a.p[4], a.rows, tile, smem_raw); break;
         }
         // release: the barrier orders every thread's stores before thread 0's
         // device-scope fence, which orders them before the count update

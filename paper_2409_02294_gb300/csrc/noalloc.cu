@@ -65,7 +65,7 @@ Layout make_layout(int nx, int ny, int nz) {
     size_t off = 0;
     for (int a = 0; a < 3; ++a) {
         L.tw[a] = off;
-        off += align256((size_t)pgb::axis_tw_list<float>(n[a]).total * sizeof(float2));
+        off += align256((size_t)pgb::axis_tw_list<float>(n[a], a == 0).total * sizeof(float2));
     }
     for (int a = 0; a < 3; ++a) {
         L.dct[a] = off;
@@ -157,7 +157,7 @@ extern "C" poisson_status poisson_solve_noalloc(int nx, int ny, int nz, double h
         tw[a] = reinterpret_cast<float2*>(base + L.tw[a]);
         dct[a] = reinterpret_cast<double*>(base + L.dct[a]);
         k_noalloc_twiddles<<<(2 * n[a] + 255) / 256, 256, 0, st>>>(tw[a], n[a]);
-        if ((e = fill_stage_twiddles<float>(reinterpret_cast<cpx<float>*>(tw[a]), n[a], st)) != cudaSuccess)
+        if ((e = fill_stage_twiddles<float>(reinterpret_cast<cpx<float>*>(tw[a]), n[a], a == 0, st)) != cudaSuccess)
             return to_status(e);
         const int e2 = (n[a] + 1) * (n[a] + 1);
         k_noalloc_dct<<<(e2 + 255) / 256, 256, 0, st>>>(dct[a], n[a]);

@@ -25,15 +25,15 @@ template <class R> __global__ void k_stage_twiddles(cpx<R>* __restrict__ tw, int
     }
 }
 
-template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, cudaStream_t st) {
-    const StageTwList L = axis_tw_list<R>(n);
+template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, bool row, cudaStream_t st) {
+    const StageTwList L = axis_tw_list<R>(n, row);
     if (L.total == 0) return cudaErrorInvalidValue;
     if (L.count == 0) return cudaSuccess;
     k_stage_twiddles<R><<<8, 256, 0, st>>>(tw, n, L);
     return cudaGetLastError();
 }
 
-template cudaError_t fill_stage_twiddles<float>(cpx<float>*, int, cudaStream_t);
-template cudaError_t fill_stage_twiddles<double>(cpx<double>*, int, cudaStream_t);
+template cudaError_t fill_stage_twiddles<float>(cpx<float>*, int, bool, cudaStream_t);
+template cudaError_t fill_stage_twiddles<double>(cpx<double>*, int, bool, cudaStream_t);
 
 }  // namespace pgb

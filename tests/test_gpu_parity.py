@@ -290,7 +290,7 @@ def test_bad_arguments_on_device(pg):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("shape", [(16, 16, 16), (48, 32, 96), (64, 128, 192), (16, 256, 48),
-                                   (32, 16, 384), (512, 16, 32), (16, 512, 16)])
+                                   (32, 16, 384), (512, 16, 32), (16, 512, 16), (16, 32, 512)])
 def test_every_kernel_variant_matches_oracle(pg, oracle_mod, shape):
     nz, ny, nx = shape
     rng = np.random.default_rng(sum(shape) + 1)
@@ -343,6 +343,20 @@ def test_fused_dataflow_solve_matches_oracle(pg, oracle_mod, n):
                 assert l2 <= TOL32[0] and mx <= TOL32[1], (mode, l2, mx)
             assert plan.sync_status() == 0
         assert np.abs(out - five).max() <= 1e-6 * np.abs(five).max()
+
+
+def test_fused_dataflow_solve_at_512_equals_the_five_pass_solve(pg):
+    # 512 is the edge whose row tiles (x passes) use a different line
+    # configuration from its column tiles
+    n = 512
+    x = torch.from_numpy(np.random.default_rng(n).standard_normal((n, n, n)).astype(np.float32)).cuda()
+    with pg.Plan(n) as plan:
+        five = plan.solve(x)
+        for mode in (1, 2):
+            plan.set_variant(5, mode)
+            out = plan.solve(x)
+            assert plan.sync_status() == 0
+            assert ((out - five).abs().max() <= 1e-6 * five.abs().max()).item(), mode
 
 
 def test_fused_mode_rejected_for_unsupported_shapes(pg):
