@@ -227,6 +227,43 @@ def test_linearity_and_translation(oracle_mod):
     assert np.abs(p1[2:, 3:, 1:] - p0[:-2, :-3, :-1]).max() < 1e-9 * np.abs(p0).max()
 
 
+def _relabelling_holds(solve, rho, hx, hy, hz, tol):
+    p = solve(rho, h=(hx, hy, hz))
+    scale = np.abs(p).max()
+    h_arr = (hz, hy, hx)  # spacing of array axes 0, 1, 2
+    for perm in [(2, 1, 0), (1, 0, 2), (0, 2, 1), (1, 2, 0)]:
+        h_new = tuple(h_arr[a] for a in perm)
+        q = solve(np.ascontiguousarray(np.transpose(rho, perm)), h=(h_new[2], h_new[1], h_new[0]))
+        if np.abs(q - np.transpose(p, perm)).max() >= tol * scale:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("route", ["solve_direct", "solve_fft"])
+def test_reflection_and_axis_relabelling(oracle_mod, route):
+    # the kernel is even along every axis: flipping rho along an axis flips
+    # Phi.  The cell average depends on the offset and the spacings only
+    # through the box they span, so relabelling the array axes together
+    # with their spacings relabels Phi's axes: a spacing tied to the wrong
+    # axis, or a transposed offset, breaks this on an anisotropic grid
+    solve = getattr(oracle_mod, route)
+    rng = np.random.default_rng(21)
+    rho = rng.standard_normal((6, 10, 12))  # [z][y][x]
+    hx, hy, hz = 0.7, 1.3, 0.9
+    p = solve(rho, h=(hx, hy, hz))
+    scale = np.abs(p).max()
+    for ax in range(3):
+        assert np.abs(solve(np.flip(rho, ax), h=(hx, hy, hz)) - np.flip(p, ax)).max() < 1e-12 * scale
+    h_arr = (hz, hy, hx)  # spacing of array axes 0, 1, 2
+    for perm in [(2, 1, 0), (1, 0, 2), (0, 2, 1), (1, 2, 0)]:
+        h_new = tuple(h_arr[a] for a in perm)
+        q = solve(np.ascontiguousarray(np.transpose(rho, perm)), h=(h_new[2], h_new[1], h_new[0]))
+        assert np.abs(q - np.transpose(p, perm)).max() < 1e-12 * scale, perm
+        # the same relabelling without its spacings is a different problem
+        q_wrong = solve(np.ascontiguousarray(np.transpose(rho, perm)), h=(hx, hy, hz))
+        assert np.abs(q_wrong - np.transpose(p, perm)).max() > 1e-3 * scale, perm
+
+
 def test_padding_length_invariance(oracle_mod):
     # any M >= 2n - 1 per axis gives the same free-space result
     rng = np.random.default_rng(2)
@@ -346,6 +383,21 @@ def test_planted_mistakes_fail_a_pin(oracle_mod, which, tmp_path):
     finally:
         oracle_mod.use_library(None)
     assert _pins_pass(oracle_mod)
+
+
+@pytest.mark.parametrize("which", [4, 5])
+def test_relabelling_pin_alone_catches_axis_mistakes(oracle_mod, which, tmp_path):
+    # transposed spacings (4) and a mirrored source index along x (5): the
+    # relabelling pin by itself fails both (a mirrored index still passes
+    # the reflection half, so it is the relabelling that catches it)
+    rho = np.random.default_rng(21).standard_normal((6, 10, 12))
+    assert _relabelling_holds(oracle_mod.solve_direct, rho, 0.7, 1.3, 0.9, 1e-12)
+    so = oracle_mod.build_planted(which, str(tmp_path))
+    oracle_mod.use_library(so)
+    try:
+        assert not _relabelling_holds(oracle_mod.solve_direct, rho, 0.7, 1.3, 0.9, 1e-9)
+    finally:
+        oracle_mod.use_library(None)
 
 
 # ---------------------------------------------------------------------------
