@@ -67,6 +67,15 @@ typedef enum {
 
 /*
  * Create a plan for an nx x ny x nz grid.
+ * Passage: Section 3 (the convolution method for potential fields on nested
+ * grids, one N^3 array per mesh level) fixes the operation; everything the
+ * method computes once per mesh level -- the Green's function k(d), its
+ * transform, the twiddle tables -- is built here, so that a solve is only
+ * the FFT passes the paper names as the performance-critical part
+ * (Section 1).  The plan's buffers are allocated once and then reused by
+ * every solve, the device-memory analogue of the paper's link-once pointer
+ * set-up (Section 2.2, host memory: the address is taken once at start-up
+ * and both sides keep using the same array).
  *  out         receives the plan handle (caller destroys it with
  *              poisson_plan_destroy).
  *  hx, hy, hz  cell spacing (> 0).   G  gravitational constant (any finite).
@@ -114,7 +123,14 @@ poisson_status poisson_plan_create_kernel(poisson_plan_t* out, int nx, int ny, i
                                           void* cuda_stream);
 
 /*
- * Phi = G * rho.  rho_dev: nx*ny*nz input values; phi_dev: nx*ny*nz outputs.
+ * Phi = G * rho.  Passage: Section 3, the convolution method of the case
+ * study (zero-padded FFT convolution: forward 3-D FFT of the padded density,
+ * multiply by the transformed Green's function, inverse FFT, crop).  The
+ * caller owns both buffers and passes their device addresses; the library
+ * neither copies nor keeps them, in the spirit of the paper's pointer
+ * linking (Section 2.2) and its C-bound interface between separately built
+ * codes (Appendix A).
+ * rho_dev: nx*ny*nz input values; phi_dev: nx*ny*nz outputs.
  * rho_dev and phi_dev may be the same buffer (rho is fully consumed before
  * phi is written).  Asynchronous on cuda_stream.  A plan holds one
  * workspace, so solves on one plan must not overlap in time (issue them on
@@ -125,7 +141,9 @@ poisson_status poisson_solve(poisson_plan_t plan, const void* rho_dev, void* phi
                              void* cuda_stream);
 
 /*
- * Adjoint solve: grad = K^T w, the gradient of L = sum(w * Phi) with
+ * Adjoint solve.  Passage: Section 3's convolution method read backwards --
+ * the paper prints no adjoint; it is the transpose of the same linear map.
+ * grad = K^T w, the gradient of L = sum(w * Phi) with
  * respect to rho (the correlation of w with the Green's function: the same
  * padded pipeline with the conjugated transform, which for this real, even
  * kernel equals the forward one).  Same layout, aliasing and error rules as
@@ -135,8 +153,11 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* w_dev, voi
                                      void* cuda_stream);
 
 /*
- * Solve `count` independent fields, plans[i] applied to rho_dev[i] ->
- * phi_dev[i].  Plans may have different sizes but must share the device
+ * Solve `count` independent fields.  Passage: Section 3, where every mesh
+ * level of the nested grid is one independent N^3 convolution solve (one
+ * level per image, and one GPU per level in the fully parallel runs); here
+ * the levels, or any list of fields, share one GPU.  plans[i] is applied to
+ * rho_dev[i] -> phi_dev[i].  Plans may have different sizes but must share the device
  * and precision (FP32); each plan appears at most once (a plan owns one
  * workspace and the fields run at the same time: use one plan per field, or
  * poisson_solve_host_levels, which serialises repeats).  Three executions exist, each replayed from a CUDA
@@ -215,7 +236,28 @@ poisson_status poisson_solve_host_levels(poisson_plan_t const* plans, int count,
 poisson_status poisson_solve_pass(poisson_plan_t plan, int pass, const void* rho_dev,
                                   void* phi_dev, void* cuda_stream);
 
-/* Release every device resource of the plan (synchronises the device). */
+/*
+ * The plain FP32 pipeline, kept as a yardstick for the fused passes.
+ * Passage: Section 3's convolution method in its straightforward form, with
+ * this library's own line transforms: the padded Mx x My x Mz grid (M = 2n
+ * per axis) is materialised as complex FP32 values, transformed by full
+ * length-M FFTs along x, y and z in three separate passes, multiplied by the
+ * transformed Green's function in a pass of its own, transformed back along
+ * z, y and x, and cropped to phi.  Nothing is pruned or fused.  Same
+ * arguments, layout and result as poisson_solve; FP32 plans only.  The
+ * first call allocates the plan's 8 Mx My Mz-byte padded buffer and its
+ * twiddle tables (kept until poisson_plan_destroy); later calls allocate
+ * nothing.  Asynchronous on cuda_stream.  Errors: POISSON_ERR_ARG (null or
+ * unaligned pointer, null plan), POISSON_ERR_UNSUPPORTED (not an FP32 plan),
+ * POISSON_ERR_ALLOC, POISSON_ERR_CUDA.
+ */
+poisson_status poisson_solve_unfused(poisson_plan_t plan, const void* rho_dev, void* phi_dev,
+                                     void* cuda_stream);
+
+/* Release every device resource of the plan (synchronises the device).
+ * Passage: the end of the plan's lifetime of Section 2.2's link-once
+ * set-up; after this call the handle must not be used again.
+ * Errors: POISSON_ERR_ARG (null plan). */
 poisson_status poisson_plan_destroy(poisson_plan_t plan);
 
 typedef struct {
@@ -295,7 +337,10 @@ poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream);
  * near-field radius.  The Green's function is rebuilt on every call.
  *
  * Limits: the grid's Green's function, tables and work buffers must fit the
- * 16 MiB array (64^3, or 128 x 64 x 64, fit; 128^3 does not); larger grids
+ * 16 MiB array: 64^3 fits, and so does nx = 128 with ny = nz = 64 (a long x
+ * axis is the only anisotropic shape with a 128 edge that fits, because the
+ * x axis' spectrum keeps only nx + 1 bins); ny = 128 or nz = 128 with the
+ * other two at 64 does not, nor does 128^3; larger grids
  * return POISSON_ERR_ARG before any work is queued.  Unsupported edge lengths
  * return POISSON_ERR_UNSUPPORTED.
  * Set-up: the first call on each device looks up the array's device address;

@@ -23,7 +23,8 @@ independent ways:
    (j*k mod M) from one table of M roots of unity.
 3. ``solve_fft``     - the same padded convolution with a library FP64 FFT
    (scipy.fft), for full fields at the large sizes; ``solve_fft_kernel``
-   with a caller's even kernel.
+   with a caller's even kernel; ``kernel_rfft`` + ``solve_fft_with`` split
+   ``solve_fft`` into its grid-only part and its per-density part.
 
 The kernel k(d) and the readings of the paper it rests on are described in
 ``oracle.c``.  Pins of every function here against values fixed by the
@@ -284,22 +285,38 @@ def solve_dft(rho, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT, M_zyx=None):
 # Route 3: library FFT
 # ----------------------------------------------------------------------------
 
-def solve_fft(rho, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT, M_zyx=None, workers=-1):
-    """The padded convolution with scipy's FP64 real FFTs."""
+def kernel_rfft(n_zyx, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT, M_zyx=None, workers=-1):
+    """The real FFT (scipy.fft.rfftn, FP64) of -G V k on the padded grid:
+    the part of ``solve_fft`` that depends only on the grid, computed once
+    when many densities of one grid are solved."""
     import scipy.fft as sfft
-    rho = np.asarray(rho, dtype=np.float64)
-    nz, ny, nx = rho.shape
+    nz, ny, nx = n_zyx
     M = M_zyx if M_zyx is not None else (2 * nz, 2 * ny, 2 * nx)
     hx, hy, hz = _h3(h)
     kw = wrapped_kernel((nz, ny, nx), M, h, r_near)
     kw *= -G * hx * hy * hz
-    Kh = sfft.rfftn(kw, workers=workers)
-    del kw
+    return sfft.rfftn(kw, workers=workers)
+
+
+def solve_fft_with(rho, Kh, M_zyx=None, workers=-1):
+    """The padded convolution of rho with the transformed kernel Kh of
+    ``kernel_rfft`` (same grid, same padding): forward real FFT of the
+    zero-padded density, multiply, inverse real FFT, crop."""
+    import scipy.fft as sfft
+    rho = np.asarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    M = M_zyx if M_zyx is not None else (2 * nz, 2 * ny, 2 * nx)
     X = sfft.rfftn(rho, s=M, workers=workers)
     X *= Kh
-    del Kh
     phi = sfft.irfftn(X, s=M, workers=workers)
     return np.ascontiguousarray(phi[:nz, :ny, :nx])
+
+
+def solve_fft(rho, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT, M_zyx=None, workers=-1):
+    """The padded convolution with scipy's FP64 real FFTs."""
+    rho = np.asarray(rho, dtype=np.float64)
+    Kh = kernel_rfft(rho.shape, h, G, r_near, M_zyx, workers)
+    return solve_fft_with(rho, Kh, M_zyx, workers)
 
 
 def solve_adjoint_direct(w, h=1.0, G=1.0, r_near=R_NEAR_DEFAULT):

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("poisson_plan_copy_greens", _I, [_P, ctypes.POINTER(_D), ctypes.c_size_t]),
     ("poisson_plan_sync_status", _I, [_P, _P]),
     ("poisson_solve_noalloc", _I, [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P]),
+    ("poisson_solve_unfused", _I, [_P, _P, _P, _P]),
     ("poisson_status_string", ctypes.c_char_p, [_I]),
     ("poisson_supported_size", _I, [_I]),
 ]
@@ -201,7 +202,8 @@ class Plan:
             raise ValueError("expected a contiguous %s tensor of shape %s" % (self.dtype, self.shape))
         if out is None:
             out = torch.empty_like(x)
-        elif tuple(out.shape) != self.shape or out.dtype != self.dtype or not out.is_contiguous():
+        elif (tuple(out.shape) != self.shape or out.dtype != self.dtype or not out.is_contiguous()
+              or not out.is_cuda or out.device != x.device):
             raise ValueError("bad output tensor")
         return out
 
@@ -217,6 +219,15 @@ class Plan:
         _check(lib().poisson_solve_adjoint(self.handle, ctypes.c_void_p(w.data_ptr()),
                                            ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
                "poisson_solve_adjoint")
+        return out
+
+    def solve_unfused(self, rho, out=None, stream=None):
+        """The plain unfused FP32 pipeline (poisson_solve_unfused): padded grid
+        materialised, full per-axis FFTs, separate multiply and crop."""
+        out = self._io(rho, out)
+        _check(lib().poisson_solve_unfused(self.handle, ctypes.c_void_p(rho.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "poisson_solve_unfused")
         return out
 
     def solve_pass(self, pass_id, rho, phi, stream=None):
@@ -305,7 +316,10 @@ def solve_host_levels(plans, rhos_host, phis_host=None, stream=None):
 
 def solve_noalloc(rho, h=1.0, G=1.0, out=None, stream=None):
     """Plan-free FP32 solve that allocates no device memory inside the
-    library (poisson_solve_noalloc); for small grids only (16 MiB scratch)."""
+    library (poisson_solve_noalloc); for small grids only (16 MiB scratch).
+    The library writes nx*ny*nz floats to `out`, so `out` must be a
+    contiguous float32 tensor of rho's shape on rho's device; the call runs
+    with rho's device current (the scratch array is looked up per device)."""
     torch = _torch()
     if not (isinstance(rho, torch.Tensor) and rho.is_cuda and rho.dtype == torch.float32
             and rho.is_contiguous() and rho.dim() == 3):
@@ -315,9 +329,14 @@ def solve_noalloc(rho, h=1.0, G=1.0, out=None, stream=None):
     nz, ny, nx = rho.shape
     if out is None:
         out = torch.empty_like(rho)
-    _check(lib().poisson_solve_noalloc(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]), float(G),
-                                       ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                       _stream_handle(stream)), "poisson_solve_noalloc")
+    elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.device == rho.device
+              and out.dtype == torch.float32 and out.is_contiguous() and tuple(out.shape) == tuple(rho.shape)):
+        raise ValueError("out must be a contiguous float32 tensor of shape %s on %s"
+                         % (tuple(rho.shape), rho.device))
+    with torch.cuda.device(rho.device):
+        _check(lib().poisson_solve_noalloc(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]), float(G),
+                                           ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                           _stream_handle(stream)), "poisson_solve_noalloc")
     return out
 
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "configs.cuh"
@@ -94,6 +95,8 @@ void free_plan(poisson_plan_s* p) {
     cudaFree(p->stage_out2);
     cudaFree(p->fused_order);
     cudaFree(p->fused_ctl);
+    cudaFree(p->unf_buf);
+    for (int a = 0; a < 3; ++a) cudaFree(p->unf_tw[a]);
     if (p->band_ready) {
         for (int k = 0; k < 8; ++k) {
             cudaStreamDestroy(p->band_stream[k]);

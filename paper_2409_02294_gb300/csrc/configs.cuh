@@ -3,8 +3,9 @@
 #pragma once
 
 #include <tuple>
+#include <type_traits>
 
-#include "passes.cuh"
+#include "passes_pk.cuh"
 
 namespace pgb {
 
@@ -72,6 +73,10 @@ template <class R> inline StageTwList axis_tw_list(int n, bool row) {
     }
 }
 
+// Fill the stage tables described by L of a table whose first 2n entries
+// (W_2n^j) are already on the device (async on st), FP32.
+cudaError_t fill_stage_twiddles_list(cpx<float>* tw, int n, const StageTwList& L, cudaStream_t st);
+
 // Fill the stage tables of an axis table whose first 2n entries (W_2n^j)
 // are already on the device (async on st); row as for axis_tw_list.
 template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, bool row, cudaStream_t st);
@@ -81,14 +86,28 @@ template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, bool row, 
 //   CTA threads; row passes (x forward, x inverse) likewise.
 template <class R> struct Variants;
 template <> struct Variants<float> {
+    // (the persistent TMA variants stay last: their Nyquist-column tiles
+    // need a second, plain launch)
     using Col = std::tuple<Var<2, 128>, Var<2, 256>, Var<1, 256>, Var<1, 512>, Var<2, 64>,
-                           Var<2, 128, 3>, Var<2, 64, 5>, Var<2, 128, 3, true>, Var<1, 256, 2, true>>;
+                           Var<2, 128, 3>, Var<2, 64, 5>, Var<2, 128, 1, false, true>,
+                           Var<2, 256, 1, false, true>, Var<2, 128, 3, false, true>,
+                           Var<2, 128, 3, true>, Var<1, 256, 2, true>>;
     using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>, Var<1, 256, 3>, Var<2, 64>, Var<2, 128, 4>>;
 };
 template <> struct Variants<double> {
     using Col = std::tuple<Var<1, 256>>;
     using Row = std::tuple<Var<1, 256>>;
 };
+// Plain variants (one tile per CTA, two lines per thread, 256-thread CTAs,
+// no register cap, no TMA): a fixed, shape-independent choice for callers
+// that do not autotune and create no tensor maps.
+constexpr int kRowVarPlain = 0;
+constexpr int kColVarPlain = 1;
+static_assert(std::is_same<std::tuple_element<kRowVarPlain, Variants<float>::Row>::type, Var<2, 256>>::value,
+              "kRowVarPlain must name the plain 256-thread row variant");
+static_assert(std::is_same<std::tuple_element<kColVarPlain, Variants<float>::Col>::type, Var<2, 256>>::value,
+              "kColVarPlain must name the plain 256-thread column variant");
+
 template <class R> constexpr int num_variants(int pass) {
     return (pass == 0 || pass == 4) ? (int)std::tuple_size<typename Variants<R>::Row>::value
                                     : (int)std::tuple_size<typename Variants<R>::Col>::value;
@@ -110,7 +129,16 @@ template <class C, class Tuple, int I = 0>
 cudaError_t launch_col_var(int var, int pass, const PassParams<typename C::R>& p, cudaStream_t st) {
     if constexpr (I < (int)std::tuple_size<Tuple>::value) {
         using V = typename std::tuple_element<I, Tuple>::type;
-        if (var == I) return launch_col<C, V>(pass, p, st);
+        if (var == I) {
+            if constexpr (V::PK) {
+                if constexpr (std::is_same<typename C::R, float>::value)
+                    return launch_col_pk<C, var_slots<C, V>(), V::MINB>(pass, p, st);
+                else
+                    return cudaErrorInvalidValue;
+            } else {
+                return launch_col<C, V>(pass, p, st);
+            }
+        }
         return launch_col_var<C, Tuple, I + 1>(var, pass, p, st);
     } else {
         return cudaErrorInvalidValue;

@@ -19,13 +19,18 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress (in host code the array's name is only a
-// host-side stand-in, not a device address) and caches it per device.  Make
-// that first call on each device before any stream capture begins.
+// host-side stand-in, not a device address) and caches it per device,
+// together with the identity of the CUDA context it was taken in; a call in
+// a new context on that device (after cudaDeviceReset, say) looks it up
+// again.  Make the first call on each device, and the first after a device
+// reset, before any stream capture begins.
 //
 // Per call (all on the caller's stream): FP64 Green's kernel octant, its
 // DCT-I along x, y, z and scaling to an FP32 octant, the twiddle tables, then
 // the same five passes as poisson_solve.  The Green's function is rebuilt on
 // every call; this entry point trades that cost for needing no plan.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -44,6 +49,32 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context id the address belongs to
+
+// Unique id of the calling thread's current CUDA context (driver entry
+// points, no link against libcuda); 0 if it cannot be read.
+unsigned long long current_context_id() {
+    static std::once_flag once;
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -111,18 +142,24 @@ poisson_status to_status(cudaError_t e) {
     return POISSON_ERR_CUDA;
 }
 
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device (set up once
+// per device and context).
 cudaError_t scratch_address(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    // before the first CUDA call of the process there may be no current
+    // context (id 0): the lookup then runs, initialises the device's primary
+    // context, and the id is read again after it
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
     return cudaSuccess;
@@ -192,7 +229,8 @@ extern "C" poisson_status poisson_solve_noalloc(int nx, int ny, int nz, double h
             case 3: p.in = w2; p.out = w1; N = ny; p.tw = reinterpret_cast<const cpx<float>*>(tw[1]); break;
             default: p.in = w1; p.out = phi_dev; N = nx; p.tw = reinterpret_cast<const cpx<float>*>(tw[0]); break;
         }
-        if ((e = launch_pass_f32(N, pass, (pass == 0 || pass == 4) ? 0 : 1, p, ny * nz, st)) != cudaSuccess)
+        if ((e = launch_pass_f32(N, pass, (pass == 0 || pass == 4) ? kRowVarPlain : kColVarPlain, p, ny * nz,
+                                 st)) != cudaSuccess)
             return to_status(e);
     }
     return POISSON_OK;

@@ -898,11 +898,13 @@ template <int PASS, class Cfg, int A, int B> struct SmemTag {};
 // A variant fixes lines per thread and the CTA's target thread count; the
 // tile width (column passes: SLOTS lines, row passes: PAIRS row pairs)
 // follows from the line's thread count T.
-template <int LPT_, int THREADS_, int MINB_ = 1, bool TMA_ = false> struct Var {
+template <int LPT_, int THREADS_, int MINB_ = 1, bool TMA_ = false, bool PK_ = false> struct Var {
     static constexpr int LPT = LPT_;
     static constexpr int THREADS = THREADS_;
     static constexpr int MINB = MINB_;  // minimum resident CTAs per SM (register cap)
     static constexpr bool TMA = TMA_;   // column passes: persistent kernel with TMA prefetch (FP32)
+    static constexpr bool PK = PK_;     // column passes: packed FP32x2 line transforms (FP32, LPT 2)
+    static_assert(!PK_ || (LPT_ == 2 && !TMA_), "packed tiles carry both halves and load from global");
 };
 
 template <class Cfg, class V> constexpr int var_slots() {

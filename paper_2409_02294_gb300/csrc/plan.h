@@ -34,6 +34,8 @@ struct poisson_plan_s {
     cudaStream_t band_stream[8];  // banded execution: one stream per kx band
     cudaEvent_t band_ev_x, band_ev_y[8], band_ev_done[8];
     bool band_ready;
+    void* unf_buf;        // poisson_solve_unfused: the padded complex grid (made on first use)
+    void* unf_tw[3];      // its per-axis W_2M tables
 };
 
 namespace pgb {

@@ -10,10 +10,12 @@
 // accumulated in FP32: 12 mma.sync per group of 8 lines.  The DFT matrix's
 // hi/lo fragments are fixed per lane and kept in registers.
 //
-// FP16 has a narrow exponent range, so each group's operands are scaled by a
-// power of two (exact) that brings the largest magnitude to ~2^14 before the
-// split and the results are scaled back; BF16 shares FP32's range and needs
-// no scaling.
+// Each group's operands are scaled by a power of two (exact) that brings the
+// largest magnitude to ~2^14 before the split, and the results are scaled
+// back.  FP16 needs it for its narrow exponent range; BF16 shares FP32's
+// range, but without it the lo parts of small values (and their products)
+// fall below FP32's normal range and are lost when the whole field is tiny
+// (a field scaled by 1e-30 lost 1e-4 of max|Phi| that way).
 //
 // Fragment layouts (PTX m16n8k16, g = lane / 4, c = lane % 4):
 //   A (16x16, row):  a0 = A[g][2c..2c+1]   a1 = A[g+8][2c..2c+1]
@@ -104,9 +106,9 @@ template <bool BF16> struct Dft16Frags {
 template <bool BF16, bool INV>
 __device__ __forceinline__ void dft16_tc(const Dft16Frags<BF16>& F, const float (&br)[4], const float (&bi)[4],
                                          float (&dr)[4], float (&di)[4]) {
-    // FP16: scale the group so that its largest magnitude is about 2^14
+    // scale the group so that its largest magnitude is about 2^14
     float s = 1.0f, inv_s = 1.0f;
-    if constexpr (!BF16) {
+    {
         float m = 0.0f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) m = fmaxf(m, fmaxf(fabsf(br[i]), fabsf(bi[i])));

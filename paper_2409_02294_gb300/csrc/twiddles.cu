@@ -33,6 +33,12 @@ template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, bool row, 
     return cudaGetLastError();
 }
 
+cudaError_t fill_stage_twiddles_list(cpx<float>* tw, int n, const StageTwList& L, cudaStream_t st) {
+    if (L.count == 0) return cudaSuccess;
+    k_stage_twiddles<float><<<8, 256, 0, st>>>(tw, n, L);
+    return cudaGetLastError();
+}
+
 template cudaError_t fill_stage_twiddles<float>(cpx<float>*, int, bool, cudaStream_t);
 template cudaError_t fill_stage_twiddles<double>(cpx<double>*, int, bool, cudaStream_t);
 

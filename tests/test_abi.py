@@ -85,6 +85,7 @@ def test_argument_errors_before_any_device_work(L):
     assert L.poisson_solve_adjoint(None, x, x, None) == 1
     assert L.poisson_solve_host(None, x, x, None) == 1
     assert L.poisson_solve_pass(None, 0, x, x, None) == 1
+    assert L.poisson_solve_unfused(None, x, x, None) == 1
     assert L.poisson_plan_destroy(None) == 1
     assert L.poisson_plan_get_info(None, None) == 1
     assert L.poisson_plan_copy_greens(None, None, 0) == 1

@@ -4,8 +4,11 @@ FP32 accumulate) against the FP64 oracle, and their adjoint.
 The stated tolerances come from the arithmetic: an FP16 hi+lo operand carries
 22 significant bits and the products accumulate in FP32, so the error stays at
 the FP32 path's level (rel-L2 <= 1e-6); a BF16 hi+lo operand carries 16 bits
-(unit roundoff 2^-17 ~ 7.6e-6 per product), so rel-L2 <= 5e-5 and max-norm
-<= 2e-4 max|Phi|.
+(unit roundoff 2^-17 ~ 7.6e-6 per product, the dropped lo*lo term ~2^-16),
+and one radix-16 stage of each z transform runs at that precision, so
+rel-L2 <= 1e-5 and max-norm <= 2e-5 max|Phi| (measured on these fields: at
+most 3.5e-6 and 4.5e-6).  Both forms scale each group by a power of two
+before the split, so the bars hold for fields scaled by 1e-30 and 1e30.
 """
 import numpy as np
 import pytest
@@ -15,7 +18,7 @@ import workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"tc_fp16x2": (1e-6, 1e-5), "tc_bf16x2": (5e-5, 2e-4)}
+TOL = {"tc_fp16x2": (1e-6, 1e-5), "tc_bf16x2": (1e-5, 2e-5)}
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +50,7 @@ def test_tensor_core_precisions_vs_oracle(pg, oracle_mod, prec, shape):
 @pytest.mark.parametrize("prec", ["tc_fp16x2", "tc_bf16x2"])
 def test_tensor_core_plummer_and_scale_range(pg, oracle_mod, prec):
     # Plummer densities spanning several decades, and the same field scaled by
-    # 1e-30 and 1e30: the per-group power-of-two scaling keeps FP16 in range
+    # 1e-30 and 1e30: the per-group power-of-two scaling keeps both forms in range
     rho, _ = workloads.plummer_spheres((128, 64, 64), count=16, seed=7)
     rho = rho.astype(np.float32)
     ref = oracle_mod.solve_fft(rho.astype(np.float64))
@@ -75,7 +78,7 @@ def test_adjoint_directional_fd_on_subblock(pg, prec):
         lm = float((w.double() * plan.solve((rho - v).contiguous()).double()).sum())
         fd = (lp - lm) / 2.0
         an = float((g.double() * v.double()).sum())
-    tol = {"fp32": 1e-5, "tc_fp16x2": 1e-5, "tc_bf16x2": 2e-4}[prec]
+    tol = {"fp32": 1e-5, "tc_fp16x2": 1e-5, "tc_bf16x2": 4e-5}[prec]
     assert fd == pytest.approx(an, rel=tol)
 
 

@@ -207,6 +207,20 @@ def test_impulse_response(oracle_mod, route):
     assert phi[-1, -1, -1] == pytest.approx(-1.0 / (math.sqrt(3.0) * (n - 1)), rel=1e-12)
 
 
+def test_fft_route_with_a_reused_kernel_transform(oracle_mod):
+    # kernel_rfft once, then solve_fft_with for several densities of the
+    # grid: each result is the direct pair sum of its own density (an
+    # anisotropic grid, so a transposed kernel or spacing fails)
+    shape, h, G = (6, 9, 7), (1.0, 0.5, 2.0), 1.3
+    Kh = oracle_mod.kernel_rfft(shape, h=h, G=G)
+    rng = np.random.default_rng(31)
+    for _ in range(3):
+        rho = rng.standard_normal(shape)
+        a = oracle_mod.solve_direct(rho, h=h, G=G)
+        b = oracle_mod.solve_fft_with(rho, Kh)
+        assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-13
+
+
 def test_linearity_and_translation(oracle_mod):
     rng = np.random.default_rng(11)
     a = rng.standard_normal((10, 10, 10))
