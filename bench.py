@@ -84,7 +84,7 @@ def pass_bytes(nx, ny, nz, rsize=4):  # rsize: bytes per real value
 
 # the sources the pass kernels (five passes, tensor-core z pass) are built
 # from: a profile's counters stay valid while these are unchanged
-KERNEL_SOURCES = ("fft_core.cuh", "passes.cuh", "configs.cuh", "tma.cuh", "tc_dft.cuh", "internal.h",
+KERNEL_SOURCES = ("fft_core.cuh", "fft_pk.cuh", "passes.cuh", "passes_pk.cuh", "configs.cuh", "tma.cuh", "tc_dft.cuh", "internal.h",
                   "twiddles.cu", "passes_f32_row.cu", "passes_f32_y.cu", "passes_f32_z.cu", "passes_f64.cu",
                   "passes_tc.cu")
 
@@ -184,12 +184,21 @@ class ClockSampler:
         return out
 
 
+_ORACLE_CACHE = {}
+
+
 def cpu_oracle_time(rho32, reps, min_seconds):
     """Time the FP64 oracle (FFT-convolution route, all host cores).  The
     kernel's transform depends only on the grid and is computed once before
     the timed solves, as a plan would; each timed solve is the forward real
-    FFT of the padded density, the multiply and the inverse FFT."""
+    FFT of the padded density, the multiply and the inverse FFT.  The last
+    input's result is kept, so that another precision of the same field
+    reuses it as its accuracy reference when reps = 0 is asked."""
     import oracle
+    key = (rho32.shape, hashlib.sha256(np.ascontiguousarray(rho32).tobytes()).hexdigest())
+    if reps == 0 and key in _ORACLE_CACHE:
+        return list(_ORACLE_CACHE[key][0]), _ORACLE_CACHE[key][1]
+    reps = max(reps, 1)
     rho = rho32.astype(np.float64)
     Kh = oracle.kernel_rfft(rho.shape, workers=-1)
     times = []
@@ -201,6 +210,8 @@ def cpu_oracle_time(rho32, reps, min_seconds):
         times.append(time.perf_counter() - t0)
         if len(times) >= 20:
             break
+    _ORACLE_CACHE.clear()
+    _ORACLE_CACHE[key] = (times, out)
     return times, out
 
 
@@ -366,19 +377,16 @@ BATCH_MODES = ["persistent kernel (k_batched)", "per-field launches in one graph
 
 
 def batch_launches(plans, mode):
-    """Kernel launches of one batched solve: one persistent kernel (mode 0),
-    or five per field, plus the plain Nyquist-column launch of each column
-    pass that uses a persistent TMA variant (the last two column variants;
-    mode 1 only, mode 2 uses the untuned variants)."""
+    """Kernel launches of one batched solve: one persistent kernel (mode 0);
+    per field, the launches one solve with the plan's variants makes,
+    counted from a captured solve (mode 1: a column pass on a persistent
+    TMA variant adds a plain launch for its Nyquist-column tiles), or five
+    (mode 2: the untuned variants)."""
     if mode == 0:
         return 1
-    n = 0
-    for p in plans:
-        inf = p.info()
-        n += 5
-        if mode == 1:
-            n += sum(1 for ps in (1, 2, 3) if inf["variant"][ps] >= inf["variant_count"][ps] - 2)
-    return n
+    if mode == 2:
+        return 5 * len(plans)
+    return sum(p.launch_count() for p in plans)
 
 
 def run_batch(args):
@@ -429,12 +437,28 @@ def run_batch(args):
         e1.record(stream)
         torch.cuda.synchronize()
         seq.append(e0.elapsed_time(e1))
-    # accuracy: batched output vs the single-field solve for every field
+    # accuracy: batched output vs the single-field solve for every field, and
+    # vs the FP64 oracle for one field of each distinct shape (up to 12)
     pg.solve_batched(plans, rhos, phis, stream)
     worst = 0.0
     for p, r, o in zip(plans, rhos, phis):
         ref = p.solve(r)
         worst = max(worst, float((o.double() - ref.double()).norm() / ref.double().norm()))
+    acc = {"max_rel_l2_vs_single_field_solve": worst}
+    if not args.no_cpu_baseline:
+        import oracle
+        seen, l2s, mxs = set(), [], []
+        for s, d, o in zip(shapes, dens, phis):
+            if s in seen or len(seen) >= 12:
+                continue
+            seen.add(s)
+            ref = oracle.solve_fft(d.astype(np.float64))
+            out = o.double().cpu().numpy()
+            l2s.append(float(np.linalg.norm(out - ref) / np.linalg.norm(ref)))
+            mxs.append(float(np.abs(out - ref).max() / np.abs(ref).max()))
+        acc.update({"rel_l2": max(l2s), "max_rel": max(mxs), "tolerance_rel_l2": TOL_REL_L2,
+                    "reference": "FP64 oracle, full field, one field of each of %d distinct shapes "
+                                 "(worst of them)" % len(seen)})
     pb = 0
     for s in shapes:
         pb += sum(pass_bytes(s[2], s[1], s[0]))
@@ -458,13 +482,12 @@ def run_batch(args):
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "algorithmic_bytes": pb, "peak_source": peak_kind},
-        "accuracy": {"max_rel_l2_vs_single_field_solve": worst},
+        "accuracy": acc,
         "gpu_launches": args.steps * batch_launches(plans, chosen),
     }
-    print(json.dumps(line))
     for p in plans:
         p.close()
-    return 0
+    return emit(line, args)
 
 
 def run_levels(args):
@@ -559,10 +582,9 @@ def run_levels(args):
                 "overlap_speedup": t_seq / t_ov, "equal_to_device_solve": same},
         "gpu_launches": launches * args.steps,
     }
-    print(json.dumps(line))
     for p in plans:
         p.close()
-    return 0
+    return emit(line, args)
 
 
 def run_ours(args):
@@ -675,7 +697,8 @@ def run_ours(args):
     cpu = None
     acc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, ref = cpu_oracle_time(rho32, reps=2, min_seconds=8.0 if nf == 1 else 0.0)
+        times, ref = cpu_oracle_time(rho32, reps=getattr(args, "cpu_reps", 2),
+                                     min_seconds=getattr(args, "cpu_min_seconds", 8.0) if nf == 1 else 0.0)
         if wl == "blobs32":
             import oracle
             ref = oracle.solve_direct(rho32.astype(np.float64))  # the exact pair sum
@@ -752,8 +775,9 @@ def run_ours(args):
             e2e["pageable_value"] = n ** 3 / tp
 
     dom = int(np.argmax(pass_ms))
+    kernel_names = list(KERNEL_NAMES)
     if args.precision in ("tc_fp16x2", "tc_bf16x2"):
-        KERNEL_NAMES[2] = "k_z_conv_tc"
+        kernel_names[2] = "k_z_conv_tc"
     pb = pass_bytes(n, n, n, 8 if args.precision == "fp64" else 4)
     peak, peak_kind = peaks()
     if fused:
@@ -763,7 +787,7 @@ def run_ours(args):
         dom_bytes = sum(pb)
         achieved = dom_bytes * nf / (total_ms / args.steps / 1e3) / 1e9
     else:
-        dom_name = KERNEL_NAMES[dom]
+        dom_name = kernel_names[dom]
         dom_bytes = pb[dom]
         achieved = pb[dom] / (pass_ms[dom] / 1e3) / 1e9
     traffic = profiled_traffic(dom_name, wl)
@@ -799,10 +823,57 @@ def run_ours(args):
             "clocks": clocks,
             "wall_s_timed": t_wall,
         }
-        print(json.dumps(line))
     plan.close()
+    del rhos, phis, rho, phi, flush
     if world > 1:
         dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    if world == 1 and args.configs:
+        line["configs"] = secondary_configs(args)
+    return emit(line, args)
+
+
+# The other configurations of the benchmark, measured in the same run after
+# the headline line (one GPU): the 32^3 FP64 direct-sum check, 256^3 Plummer,
+# the 96-field uneven batch, 8 x 384^3 Plummer in FP32 and both
+# compensated tensor-core precisions, and the nested-grid levels.
+SECONDARY = [("blobs32", "fp64"), ("plummer256", "fp32"), ("batch96", "fp32"), ("plummer384x8", "fp32"),
+             ("plummer384x8", "tc_fp16x2"), ("plummer384x8", "tc_bf16x2"), ("nested128x8", "fp32")]
+DROP_KEYS = ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data",
+             "library_baselines_same_gpu", "host_transfer_128cube_fp64", "e2e", "kernel_variants")
+
+
+def secondary_configs(args):
+    import copy
+    import gc
+
+    import torch
+    out = {}
+    for wl, prec in SECONDARY:
+        a = copy.copy(args)
+        a.workload, a.precision = wl, prec
+        a.steps, a.warmup = max(5, min(args.steps, 20)), 3
+        a.no_e2e, a.no_baselines, a.variants, a.configs, a.quiet = True, True, "", False, True
+        # the oracle here gives the accuracy reference (computed once per field)
+        a.cpu_reps, a.cpu_min_seconds = 0, 0.0
+        key = wl if prec == "fp32" else "%s_%s" % (wl, prec)
+        t0 = time.perf_counter()
+        try:
+            line = RUNNERS.get(wl, run_ours)(a)
+            out[key] = {k: v for k, v in line.items() if k not in DROP_KEYS}
+        except Exception as exc:  # report, keep the headline line
+            out[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        out[key]["wall_s"] = time.perf_counter() - t0
+        gc.collect()
+        torch.cuda.empty_cache()
+    return out
+
+
+def emit(line, args):
+    if getattr(args, "quiet", False):
+        return line
+    print(json.dumps(line))
     return 0
 
 
@@ -820,17 +891,21 @@ def main():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--variants", default="",
                     help="comma list of kernel variants per pass (and execution mode): skip autotuning")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="measure only the headline workload (by default the other configurations are "
+                         "measured after it and reported under 'configs')")
     args = ap.parse_args()
+    args.quiet = False
+    if args.workload != "lognormal512" or args.variants:
+        args.configs = False
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch96":
-        return run_batch(args)
-    if args.workload == "nested128x8":
-        return run_levels(args)
-    return run_ours(args)
+    return RUNNERS.get(args.workload, run_ours)(args)
 
+
+RUNNERS = {"batch96": run_batch, "nested128x8": run_levels}
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -87,11 +87,12 @@ template <class R> cudaError_t fill_stage_twiddles(cpx<R>* tw, int n, bool row, 
 template <class R> struct Variants;
 template <> struct Variants<float> {
     // (the persistent TMA variants stay last: their Nyquist-column tiles
-    // need a second, plain launch)
+    // need a second, plain launch; the last two double-buffer, the one
+    // before them single-buffers its 16-column tiles)
     using Col = std::tuple<Var<2, 128>, Var<2, 256>, Var<1, 256>, Var<1, 512>, Var<2, 64>,
-                           Var<2, 128, 3>, Var<2, 64, 5>, Var<2, 128, 1, false, true>,
-                           Var<2, 256, 1, false, true>, Var<2, 128, 3, false, true>,
-                           Var<2, 128, 3, true>, Var<1, 256, 2, true>>;
+                           Var<2, 128, 3>, Var<2, 64, 5>, Var<2, 128, 1, 0, true>,
+                           Var<2, 256, 1, 0, true>, Var<2, 128, 3, 0, true>,
+                           Var<2, 256, 1, 1>, Var<2, 128, 3, 2>, Var<1, 256, 2, 2>>;
     using Row = std::tuple<Var<2, 256>, Var<1, 256>, Var<2, 128>, Var<1, 256, 3>, Var<2, 64>, Var<2, 128, 4>>;
 };
 template <> struct Variants<double> {

@@ -791,13 +791,16 @@ __global__ void __launch_bounds__(row_threads<Cfg, PAIRS, LPT>(), MINB) k_x_inv(
 //
 // Each CTA walks tiles t0 + blockIdx.x, + gridDim.x, ... of [t0, t1).  A
 // tile's input (ROWS rows x SLOTS columns) is one 3-D box of the W1/W2 array
-// (up to 256 rows per TMA copy), copied into one of two shared-memory
+// (up to 256 rows per TMA copy), copied into one of NBUF shared-memory
 // buffers; once every thread holds tile i in registers, thread 0 starts the
-// copy of tile i+2 into the buffer tile i came from, so two tiles' loads are
-// always in flight under the transforms.  Box layouts in shared memory:
+// copy of tile i+NBUF into the buffer tile i came from, so NBUF tiles' loads
+// are in flight under the transforms.  NBUF = 1 is for the long columns
+// (384, 512), where one CTA per SM holds a 16-column tile: its next tile's
+// load then overlaps the current tile's transforms and stores instead of
+// following them.  Box layouts in shared memory:
 //   y passes (PASS 1, 3): [other][row][kx]   (other = z, outermost dim)
 //   z pass (PASS 2):      [row][other][kx]   (other = ky line, middle dim)
-template <int PASS, class Cfg, int SLOTS> struct TmaBox {
+template <int PASS, class Cfg, int SLOTS, int NBUF> struct TmaBox {
     static constexpr int ROWS = PASS == 3 ? 2 * Cfg::N : Cfg::N;
     static constexpr int XW = SLOTS < Seg<float>::XW ? SLOTS : Seg<float>::XW;
     static constexpr int NLW = SLOTS / XW;
@@ -805,19 +808,21 @@ template <int PASS, class Cfg, int SLOTS> struct TmaBox {
     static constexpr int CH = ROWS <= 256 ? ROWS : ROWS % 256 == 0 ? 256 : ROWS % 192 == 0 ? 192 : 128;
     static constexpr int NCH = ROWS / CH;
     static constexpr unsigned BYTES = (unsigned)ROWS * SLOTS * 8u;  // one buffer
-    static constexpr size_t WORK_OFF = 2ull * BYTES + 128;          // two mbarriers, then the work area
+    static constexpr size_t WORK_OFF = (size_t)NBUF * BYTES + 128;  // NBUF mbarriers, then the work area
+    static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
     static_assert(ROWS % CH == 0, "rows must split into whole copies");
-    static_assert(NCH == 1 || NLW == 1, "more than 256 rows needs one line per box column");
+    // more than 256 rows needs one line per box column
+    static constexpr bool LAYOUT_OK = NCH == 1 || NLW == 1;
 };
 constexpr int kTmaWaitPolls = 1 << 20;  // bounded wait for one tile's copy
 
-template <int PASS, class Cfg, int SLOTS, int LPT, int MINB>
+template <int PASS, class Cfg, int SLOTS, int LPT, int MINB, int NBUF>
 __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
     k_col_tma(PassParams<float> p, const __grid_constant__ CUtensorMap map, int t0, int t1, int hold) {
-    using B = TmaBox<PASS, Cfg, SLOTS>;
+    using B = TmaBox<PASS, Cfg, SLOTS, NBUF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* buf = reinterpret_cast<cpx<float>*>(smem_raw);  // buffer k at buf + k * ROWS * SLOTS
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * B::BYTES);  // bar[0], bar[1]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NBUF * B::BYTES);  // bar[0 .. NBUF)
     unsigned char* work = smem_raw + B::WORK_OFF;
     const int lines = PASS == 2 ? 2 * p.ny : p.nz;
     const int wide_l = (lines + B::NLW - 1) / B::NLW;
@@ -833,8 +838,8 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
         }
     };
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
+#pragma unroll
+        for (int k = 0; k < NBUF; ++k) mbar_init(bar + k, 1);
         mbar_fence_init();
     }
     __syncthreads();
@@ -843,25 +848,25 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
     const int G = (int)gridDim.x;
     if (threadIdx.x == 0) {
         if (!hold) issue(tile, 0);  // test hook: the first copy is never issued, its wait runs out
-        if (tile + G < t1) issue(tile + G, 1);
+        if (NBUF == 2 && tile + G < t1) issue(tile + G, 1);
     }
     const int slot = threadIdx.x % SLOTS;
     const int off = PASS == 2 ? slot : (slot / B::XW) * B::ROWS * B::XW + slot % B::XW;
     const int stride = PASS == 2 ? SLOTS : B::XW;
     unsigned parity = 0;  // bit k: phase parity of bar[k]
-    for (int k = 0; tile < t1; tile += G, k ^= 1) {
+    for (int k = 0; tile < t1; tile += G, k = NBUF == 2 ? k ^ 1 : 0) {
         const bool ok = __syncthreads_and(mbar_wait(bar + k, (parity >> k) & 1u, kTmaWaitPolls));
         if (!ok) {
             // record the timeout, give the copies in flight a last bounded
             // chance to land, and leave (uniformly for the whole CTA)
             if (threadIdx.x == 0 && p.status) atomicOr(p.status, 2u);
             (void)mbar_wait(bar + k, (parity >> k) & 1u, kTmaWaitPolls);
-            if (tile + G < t1) (void)mbar_wait(bar + (k ^ 1), (parity >> (k ^ 1)) & 1u, kTmaWaitPolls);
+            if (NBUF == 2 && tile + G < t1) (void)mbar_wait(bar + (k ^ 1), (parity >> (k ^ 1)) & 1u, kTmaWaitPolls);
             return;
         }
         parity ^= 1u << k;
         const ColFromSmem<float> in{buf + k * B::ROWS * SLOTS + off, stride};
-        const int next = tile + 2 * G;
+        const int next = tile + NBUF * G;
         auto hook = [&]() {
             __syncthreads();  // every thread has its inputs: buffer k is free
             if (threadIdx.x == 0 && next < t1) {
@@ -898,11 +903,11 @@ template <int PASS, class Cfg, int A, int B> struct SmemTag {};
 // A variant fixes lines per thread and the CTA's target thread count; the
 // tile width (column passes: SLOTS lines, row passes: PAIRS row pairs)
 // follows from the line's thread count T.
-template <int LPT_, int THREADS_, int MINB_ = 1, bool TMA_ = false, bool PK_ = false> struct Var {
+template <int LPT_, int THREADS_, int MINB_ = 1, int TMA_ = 0, bool PK_ = false> struct Var {
     static constexpr int LPT = LPT_;
     static constexpr int THREADS = THREADS_;
     static constexpr int MINB = MINB_;  // minimum resident CTAs per SM (register cap)
-    static constexpr bool TMA = TMA_;   // column passes: persistent kernel with TMA prefetch (FP32)
+    static constexpr int TMA = TMA_;    // column passes: persistent kernel with TMA prefetch into TMA_ (1, 2) buffers (FP32)
     static constexpr bool PK = PK_;     // column passes: packed FP32x2 line transforms (FP32, LPT 2)
     static_assert(!PK_ || (LPT_ == 2 && !TMA_), "packed tiles carry both halves and load from global");
 };
@@ -957,18 +962,23 @@ cudaError_t launch_row(int pass, const PassParams<typename Cfg::R>& p, int rows,
 // Host side of k_col_tma: tensor map of the pass's input array, grid of at
 // most the resident CTAs, then the narrow tiles (Nyquist column, not a TMA
 // box) through the plain kernel.
-template <int PASS, class Cfg, int S, int L, int MINB>
+template <int PASS, class Cfg, int S, int L, int MINB, int NBUF>
 cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, int n_wide, cudaStream_t st) {
-    using B = TmaBox<PASS, Cfg, S>;
+    using B = TmaBox<PASS, Cfg, S, NBUF>;
     constexpr int NT = col_threads<Cfg, S, L>();
     constexpr size_t work = PASS == 2 ? col_smem_z<Cfg, S>() : col_smem<Cfg, S>();
     constexpr size_t sm = B::WORK_OFF + work;
+    // a tile whose buffers do not fit one CTA's shared memory (e.g. the
+    // single-buffered inverse y pass of 512 rows, two halves), or whose box
+    // would need more than 256 rows and several lines per box column, runs
+    // every tile through the plain kernel instead
+    constexpr bool fits = B::LAYOUT_OK && sm <= 227u * 1024u;
     cudaError_t e;
-    const int w1 = t_end < n_wide ? t_end : n_wide;
-    if (t_begin < w1) {
-        auto kern = k_col_tma<PASS, Cfg, S, L, MINB>;
-        if ((e = set_smem<SmemTag<40 + PASS, Cfg, S, L * 16 + MINB>>(kern, sm)) != cudaSuccess) return e;
-        static int per_sm[64] = {};  // resident CTAs per SM, per device
+    const int w1 = fits ? (t_end < n_wide ? t_end : n_wide) : t_begin;
+    if constexpr (fits) if (t_begin < w1) {
+        auto kern = k_col_tma<PASS, Cfg, S, L, MINB, NBUF>;
+        if ((e = set_smem<SmemTag<40 + 10 * NBUF + PASS, Cfg, S, L * 16 + MINB>>(kern, sm)) != cudaSuccess) return e;
+        static int per_sm[64] = {};  // resident CTAs on the device, per device
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         const int d = dev < 64 ? dev : 63;
@@ -997,7 +1007,7 @@ cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, i
         kern<<<grid, NT, sm, st>>>(p, map, t_begin, w1, hold && hold[0] == '1' ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int n0 = t_begin > n_wide ? t_begin : n_wide;
+    const int n0 = !fits ? t_begin : (t_begin > n_wide ? t_begin : n_wide);
     if (n0 < t_end) {
         PassParams<float> q = p;
         q.tile0 = n0;
@@ -1036,9 +1046,9 @@ cudaError_t launch_col(int pass, const PassParams<typename Cfg::R>& p, cudaStrea
         const int total = col_grid<R, S>(p.nx + 1, lines);
         const int n_wide = col_wide_tiles<R, S>(p.nx + 1, lines);
         const int tb = p.tile0, te = p.ntile > 0 ? p.tile0 + p.ntile : total;
-        if (pass == 1) return launch_col_tma<1, Cfg, S, V::LPT, V::MINB>(p, tb, te, n_wide, st);
-        if (pass == 3) return launch_col_tma<3, Cfg, S, V::LPT, V::MINB>(p, tb, te, n_wide, st);
-        return launch_col_tma<2, Cfg, S, V::LPT, V::MINB>(p, tb, te, n_wide, st);
+        if (pass == 1) return launch_col_tma<1, Cfg, S, V::LPT, V::MINB, V::TMA>(p, tb, te, n_wide, st);
+        if (pass == 3) return launch_col_tma<3, Cfg, S, V::LPT, V::MINB, V::TMA>(p, tb, te, n_wide, st);
+        return launch_col_tma<2, Cfg, S, V::LPT, V::MINB, V::TMA>(p, tb, te, n_wide, st);
     }
     constexpr int S = var_slots<Cfg, V>();
     constexpr int L = V::LPT;

@@ -458,15 +458,17 @@ def test_autotune_result_is_reused_for_the_same_shape(pg, oracle_mod):
     assert l2 <= TOL32[0] and mx <= TOL32[1]
 
 
-def test_tma_column_kernel_wait_timeout_is_reported(pg, oracle_mod, monkeypatch):
+@pytest.mark.parametrize("from_last", [3, 2])
+def test_tma_column_kernel_wait_timeout_is_reported(pg, oracle_mod, monkeypatch, from_last):
     # Test hook: the persistent TMA kernel skips its first copy, so the bounded
     # mbarrier wait (about a second) runs out; the kernel records a timeout in
-    # the status word and returns, and the GPU stays usable.
+    # the status word and returns, and the GPU stays usable.  from_last = 3:
+    # the single-buffered variant, 2: the first double-buffered one.
     shape = (32, 32, 32)
     rho = np.random.default_rng(31).standard_normal(shape).astype(np.float32)
     x = torch.from_numpy(rho).cuda()
     with pg.Plan(32) as plan:
-        tma = plan.info()["variant_count"][2] - 2  # first persistent TMA column variant
+        tma = plan.info()["variant_count"][2] - from_last  # a persistent TMA column variant
         plan.set_variant(2, tma)
         monkeypatch.setenv("POISSON_TEST_TMA_HOLD", "1")
         plan.solve(x)
