@@ -10,9 +10,10 @@ Public entry points mirror the C-ABI of ``include/poisson.h``:
 * ``Plan(nx, ny, nz, h=1.0, G=1.0, precision="fp32")`` -
   ``poisson_plan_create``; ``.solve(rho)``, ``.adjoint(w)``,
   ``.solve_host(rho_host)``, ``.solve_pass(i, rho, phi)``,
-  ``.greens_octant()``, ``.info()``, ``.close()``
+  ``.solve_unfused(rho)``, ``.greens_octant()``, ``.info()``, ``.close()``
 * ``solve_batched(plans, rhos, phis)`` - ``poisson_solve_batched``
 * ``solve_host_levels(plans, rhos_host)`` - ``poisson_solve_host_levels``
+* ``solve_noalloc(rho, h, G)`` - ``poisson_solve_noalloc`` (no device allocation)
 * ``PoissonSolve`` - torch.autograd.Function (forward solve, backward adjoint)
 """
 from . import abi  # noqa: F401
@@ -24,8 +25,9 @@ from .abi import (  # noqa: F401
     lib,
     solve_batched,
     solve_host_levels,
+    solve_noalloc,
     supported_size,
 )
 
 __all__ = ["Plan", "PoissonError", "PoissonSolve", "batch_mode", "lib", "solve_batched", "solve_host_levels",
-           "supported_size"]
+           "solve_noalloc", "supported_size"]

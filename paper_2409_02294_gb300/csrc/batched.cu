@@ -11,11 +11,14 @@
 //          tuned for a field alone on the GPU are not always the best ones
 //          when fields share it.
 //
-// Work items are tiles of the five passes of every field.  The queue is laid
-// out pass-major (all x-forward tiles, then all y-forward tiles, ...) with
-// larger fields first inside a pass.  CTAs claim items with an atomic
-// counter; a tile of pass p of field f first waits until every tile of pass
-// p-1 of field f has finished (per-(field, pass) completion counters).  A
+// Work items are runs of up to GROUP consecutive tiles of one pass of one
+// field (fewer for small passes, so that every pass still splits into many
+// items).  The queue is laid out pass-major (all x-forward items, then all
+// y-forward items, ...) with larger fields first inside a pass.  CTAs claim
+// items with an atomic counter; an item of pass p of field f first waits
+// until every tile of pass p-1 of field f has finished (per-(field, pass)
+// completion counters, counted in tiles), and publishes its own tiles with
+// one release after the last of them.  A
 // wait only ever targets items earlier in the queue, which were claimed by
 // CTAs that are already running, so the scheme cannot deadlock however many
 // CTAs are resident.  Every wait is bounded: after `spin_limit` polls it sets
@@ -49,8 +52,15 @@ struct BatchField {
 };
 
 struct BatchSeg {
-    int field, pass, begin, ntiles;
+    int field, pass;
+    int begin;   // first work item of the segment
+    int ntiles;  // tiles of this pass of this field
+    int group;   // tiles per work item (the last item may hold fewer)
 };
+
+// Tiles per work item for a pass of `ntiles` tiles: up to 8, while keeping
+// at least about a thousand items in the pass.
+inline int seg_group(int ntiles) { return std::max(1, std::min(8, ntiles / 1024)); }
 
 struct BatchArgs {
     const BatchField* fields;
@@ -133,6 +143,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batched(BatchArgs a) {
         }
         const BatchSeg sg = a.segs[lo];
         const BatchField& f = a.fields[sg.field];
+        const int t_first = (w - sg.begin) * sg.group;
+        const int t_count = min(sg.group, sg.ntiles - t_first);
         if (threadIdx.x == 0) {
             bool ok = true;
             const int key = sg.field * 5 + sg.pass - 1;
@@ -147,26 +159,29 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batched(BatchArgs a) {
         }
         __syncthreads();
         if (!s_ok) return;  // timeout or abort: the whole CTA leaves together
-        const int tile = w - sg.begin;
         const PassParams<float>& p = f.p[sg.pass];
-        switch (f.N[sg.pass]) {
-            case 16: batch_tile<16>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 32: batch_tile<32>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 48: batch_tile<48>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 64: batch_tile<64>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 96: batch_tile<96>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 128: batch_tile<128>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 192: batch_tile<192>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 256: batch_tile<256>(sg.pass, p, f.rows, tile, smem_raw); break;
-            case 384: batch_tile<384>(sg.pass, p, f.rows, tile, smem_raw); break;
-            default: batch_tile<512>(sg.pass, p, f.rows, tile, smem_raw); break;
+        for (int i = 0; i < t_count; ++i) {
+            if (i > 0) __syncthreads();  // the previous tile is done with shared memory
+            const int tile = t_first + i;
+            switch (f.N[sg.pass]) {
+                case 16: batch_tile<16>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 32: batch_tile<32>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 48: batch_tile<48>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 64: batch_tile<64>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 96: batch_tile<96>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 128: batch_tile<128>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 192: batch_tile<192>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 256: batch_tile<256>(sg.pass, p, f.rows, tile, smem_raw); break;
+                case 384: batch_tile<384>(sg.pass, p, f.rows, tile, smem_raw); break;
+                default: batch_tile<512>(sg.pass, p, f.rows, tile, smem_raw); break;
+            }
         }
         // release: the barrier orders every thread's stores before thread 0's
         // device-scope fence, which orders them before the count update
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(a.ctl + 2 + sg.field * 5 + sg.pass, 1u);
+            atomicAdd(a.ctl + 2 + sg.field * 5 + sg.pass, (unsigned)t_count);
         }
     }
 }
@@ -312,11 +327,11 @@ cudaError_t build_state(BatchState* b) {
     int total = 0;
     for (int pass = 0; pass < 5; ++pass)
         for (int i : order) {
-            BatchSeg s{i, pass, total, b->h_fields[i].ntiles[pass]};
-            if (s.ntiles > 0) {
-                segs.push_back(s);
-                total += s.ntiles;
-            }
+            const int nt = b->h_fields[i].ntiles[pass];
+            if (nt <= 0) continue;
+            const BatchSeg s{i, pass, total, nt, seg_group(nt)};
+            segs.push_back(s);
+            total += (nt + s.group - 1) / s.group;  // work items of the segment
         }
     if ((e = cudaMalloc(&b->d_segs, segs.size() * sizeof(BatchSeg)))) return e;
     if ((e = cudaMemcpy(b->d_segs, segs.data(), segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice)))

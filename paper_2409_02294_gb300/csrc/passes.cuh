@@ -434,6 +434,15 @@ template <class R> struct RowPad { static constexpr int SHIFT = sizeof(R) == 4 ?
 template <class Cfg> constexpr int row_line_stride() {
     return Cfg::N + (Cfg::N >> RowPad<typename Cfg::R>::SHIFT);
 }
+// Offset (complex elements) of row pair pr's line for half h in a row
+// tile's exchange area.  The odd halves start 64 bytes further on: the
+// x-forward spectrum separation has neighbouring lanes read the even and the
+// odd line of a pair at the same index, which without the skew fall on the
+// same banks.
+template <class Cfg> constexpr int row_odd_skew() { return 64 / (int)sizeof(cpx<typename Cfg::R>); }
+template <class Cfg, int PAIRS> __device__ __forceinline__ int row_line_off(int half, int pr) {
+    return (half * PAIRS + pr) * row_line_stride<Cfg>() + half * row_odd_skew<Cfg>();
+}
 // real staging row stride: skews consecutive pairs' rows across banks
 template <class Cfg> constexpr int row_stage_stride() {
     return Cfg::N + (Cfg::T >= 8 ? Cfg::T / 2 : 4);
@@ -458,7 +467,6 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
                                             unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    constexpr int LS = row_line_stride<Cfg>();
     constexpr int RS = row_stage_stride<Cfg>();
     constexpr int SH = RowPad<R>::SHIFT;
     constexpr int NT = row_threads<Cfg, PAIRS, LPT>();
@@ -523,7 +531,7 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
     }
     LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = {sm + (id.half(l) * PAIRS + pr) * LS, 1, SH, 1};
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + row_line_off<Cfg, PAIRS>(id.half(l), pr), 1, SH, 1};
     line_fft<R, N, E, false, LPT>(v, t, ls, p.tw, typename Cfg::Rads{});
 #pragma unroll
     for (int l = 0; l < LPT; ++l)
@@ -541,8 +549,8 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
     constexpr int U = NT / PAIRS;
     const int u = t + (LPT == 1 ? id.q * T : 0);
     if (has_a) {
-        const LineSmem<R> e = {sm + pr * LS, 1, SH, 1};
-        const LineSmem<R> o = {sm + (PAIRS + pr) * LS, 1, SH, 1};
+        const LineSmem<R> e = {sm + row_line_off<Cfg, PAIRS>(0, pr), 1, SH, 1};
+        const LineSmem<R> o = {sm + row_line_off<Cfg, PAIRS>(1, pr), 1, SH, 1};
         cpx<R>* ra = out + (long long)(r0 + 2 * pr) * sx;
         cpx<R>* rb = ra + sx;
         for (int k = u; k <= N; k += U) {
@@ -587,7 +595,6 @@ __device__ __forceinline__ void tile_x_inv_direct(const PassParams<typename Cfg:
                                                    unsigned char* smem_raw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    constexpr int LS = row_line_stride<Cfg>();
     constexpr int SH = RowPad<R>::SHIFT;
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     const RowIds<Cfg, PAIRS, 2> id;
@@ -621,7 +628,7 @@ __device__ __forceinline__ void tile_x_inv_direct(const PassParams<typename Cfg:
     }
     LineSmem<R> ls[2];
 #pragma unroll
-    for (int l = 0; l < 2; ++l) ls[l] = {sm + (l * PAIRS + pr) * LS, 1, SH, 1};
+    for (int l = 0; l < 2; ++l) ls[l] = {sm + row_line_off<Cfg, PAIRS>(l, pr), 1, SH, 1};
     line_fft<R, N, E, true, 2>(v, t, ls, p.tw, typename Cfg::Rads{});
 
     // x[j] = a[j] + W_2N^-j b[j]: real part -> row 2 pr, imaginary -> row 2 pr + 1
@@ -648,7 +655,6 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
     }
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    constexpr int LS = row_line_stride<Cfg>();
     constexpr int RS = row_stage_stride<Cfg>();
     constexpr int SH = RowPad<R>::SHIFT;
     constexpr int NT = row_threads<Cfg, PAIRS, LPT>();
@@ -705,7 +711,7 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
 
     LineSmem<R> ls[LPT];
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = {sm + (id.half(l) * PAIRS + pr) * LS, 1, SH, 1};
+    for (int l = 0; l < LPT; ++l) ls[l] = {sm + row_line_off<Cfg, PAIRS>(id.half(l), pr), 1, SH, 1};
     line_fft<R, N, E, true, LPT>(v, t, ls, p.tw, typename Cfg::Rads{});
 
     // z[j] = a[j] + W_2N^-j b[j]
@@ -714,7 +720,7 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
 #pragma unroll
         for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + t + T * m));
     } else {
-        const LineSmem<R> lodd = {sm + (PAIRS + pr) * LS, 1, SH, 1};
+        const LineSmem<R> lodd = {sm + row_line_off<Cfg, PAIRS>(1, pr), 1, SH, 1};
         if (id.q) {
 #pragma unroll
             for (int m = 0; m < E; ++m) {
@@ -931,7 +937,7 @@ template <class Cfg, int SLOTS> constexpr size_t col_smem_z() {
 }
 template <class Cfg, int PAIRS> constexpr size_t row_smem() {
     using R = typename Cfg::R;
-    constexpr size_t lines = 2ull * PAIRS * row_line_stride<Cfg>() * sizeof(cpx<R>);
+    constexpr size_t lines = (2ull * PAIRS * row_line_stride<Cfg>() + row_odd_skew<Cfg>()) * sizeof(cpx<R>);
     constexpr size_t stage_c = 2ull * PAIRS * (Cfg::N + 1) * sizeof(cpx<R>);
     constexpr size_t stage_r = 2ull * PAIRS * row_stage_stride<Cfg>() * sizeof(R);
     constexpr size_t m1 = lines > stage_c ? lines : stage_c;
