@@ -891,6 +891,9 @@ def main():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--variants", default="",
                     help="comma list of kernel variants per pass (and execution mode): skip autotuning")
+    ap.add_argument("--grid", default="",
+                    help="NXxNYxNZ: time the passes of one plan on this grid (seeded normal density), "
+                         "for profiling a kernel on a smaller case")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="measure only the headline workload (by default the other configurations are "
                          "measured after it and reported under 'configs')")
@@ -902,7 +905,57 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.grid:
+        return run_grid(args)
     return RUNNERS.get(args.workload, run_ours)(args)
+
+
+def run_grid(args):
+    """One plan on an arbitrary grid (--grid NXxNYxNZ) with a seeded
+    standard-normal density: per-pass CUDA-event times and HBM fractions of
+    the five passes.  For profiling a pass kernel of a given transform length
+    on a grid smaller than the benchmark's (e.g. the 512-long z columns on
+    256 x 256 x 512)."""
+    import torch
+
+    import paper_2409_02294_gb300 as pg
+    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(args.seed)
+    rho = torch.from_numpy(rng.standard_normal((nz, ny, nx)).astype(np.float32)).cuda()
+    phi = torch.empty_like(rho)
+    if args.variants:
+        plan = pg.Plan(nx, ny, nz)
+        for i, v in enumerate(int(x) for x in args.variants.split(",")):
+            plan.set_variant(i, v)
+    else:
+        plan = pg.Plan(nx, ny, nz, flags=pg.abi.FLAG_AUTOTUNE)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        flush.zero_()
+        for i in range(5):
+            plan.solve_pass(i, rho, phi, stream)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for ev in evs:
+        flush.zero_()
+        ev[0].record(stream)
+        for i in range(5):
+            plan.solve_pass(i, rho, phi, stream)
+            ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    pass_ms = [statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in evs) for i in range(5)]
+    step_ms = statistics.mean(ev[0].elapsed_time(ev[5]) for ev in evs)
+    pb = pass_bytes(nx, ny, nz)
+    peak, _ = peaks()
+    line = {"metric": METRIC, "value": nx * ny * nz / (step_ms / 1e3), "unit": UNIT, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grid %dx%dx%d (seeded normal density)" % (nx, ny, nz)},
+            "passes": {PASS_NAMES[i]: {"ms": pass_ms[i], "frac": pb[i] / (pass_ms[i] / 1e3) / 1e9 / peak}
+                       for i in range(5)},
+            "kernel_variants": plan.info()["variant"]}
+    plan.close()
+    return emit(line, args)
 
 
 RUNNERS = {"batch96": run_batch, "nested128x8": run_levels}
