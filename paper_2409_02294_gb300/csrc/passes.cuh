@@ -383,8 +383,11 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     }
 }
 
-// pass 3: inverse FFT along y + crop.  W2 -> W1.
-template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
+// pass 3: inverse FFT along y + crop.  W2 -> W1.  SEQ (two lines per
+// thread): the even and odd halves are transformed one after the other
+// through one exchange buffer, which halves the tile's work area (the
+// single-buffered persistent TMA tile of 512-long columns then fits).
+template <class Cfg, int SLOTS, int LPT, bool CG, bool SEQ = false, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p, int tile,
                                             unsigned char* smem_raw, const In& in_src = In{},
                                             const Hook& after_load = Hook{}) {
@@ -409,10 +412,25 @@ __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p,
                               : cpx<R>{0, 0};
     }
     after_load();
-    LineSmem<R> ls[LPT];
+    if constexpr (SEQ && LPT == 2) {
+        const LineSmem<R> l0[1] = {col_line<R, N, SLOTS>(sm, 0, id.slot)};
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
-    line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
+        for (int l = 0; l < 2; ++l) {
+            cpx<R> u[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) u[0][m] = v[l][m];
+            // the previous transform's last shared-memory read ended with a
+            // barrier, so this one may write the buffer at once
+            line_fft<R, N, E, true, 1>(u, id.t, l0, p.tw, typename Cfg::Rads{});
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[l][m] = u[0][m];
+        }
+    } else {
+        LineSmem<R> ls[LPT];
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
+        line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
+    }
 
     if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
         cpx<R>* dst = out + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
@@ -882,7 +900,7 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
         };
         if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
         else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
-        else tile_y_inv<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
+        else tile_y_inv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(p, tile, work, in, hook);
     }
 }
 
@@ -972,10 +990,12 @@ template <int PASS, class Cfg, int S, int L, int MINB, int NBUF>
 cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, int n_wide, cudaStream_t st) {
     using B = TmaBox<PASS, Cfg, S, NBUF>;
     constexpr int NT = col_threads<Cfg, S, L>();
-    constexpr size_t work = PASS == 2 ? col_smem_z<Cfg, S>() : col_smem<Cfg, S>();
+    // (the single-buffered inverse y tile transforms its halves one after the
+    // other through one exchange buffer: half the work area)
+    constexpr size_t work = PASS == 2 ? col_smem_z<Cfg, S>()
+                                      : (PASS == 3 && NBUF == 1 && L == 2 ? col_smem<Cfg, S>() / 2 : col_smem<Cfg, S>());
     constexpr size_t sm = B::WORK_OFF + work;
-    // a tile whose buffers do not fit one CTA's shared memory (e.g. the
-    // single-buffered inverse y pass of 512 rows, two halves), or whose box
+    // a tile whose buffers do not fit one CTA's shared memory, or whose box
     // would need more than 256 rows and several lines per box column, runs
     // every tile through the plain kernel instead
     constexpr bool fits = B::LAYOUT_OK && sm <= 227u * 1024u;
