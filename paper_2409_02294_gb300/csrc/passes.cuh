@@ -184,6 +184,38 @@ __device__ __forceinline__ cpx<R> col_in(const ColFromSmem<R>& s, const cpx<R>*,
     return s.base[row * s.stride];
 }
 
+// Transform the LPT register lines of a column thread (forward or inverse).
+// SEQ (two lines per thread): the even and odd halves go one after the other
+// through the first exchange buffer, so the tile needs one buffer instead of
+// two (each transform's last shared-memory read ends with a barrier, so the
+// next may write the buffer at once); otherwise both halves run in lockstep,
+// each through its own buffer.
+template <class Cfg, int SLOTS, int LPT, bool SEQ, bool INV>
+__device__ __forceinline__ void col_line_ffts(cpx<typename Cfg::R> (&v)[LPT][Cfg::E], const ColIds<Cfg, SLOTS, LPT>& id,
+                                              cpx<typename Cfg::R>* sm, const cpx<typename Cfg::R>* tw) {
+    using R = typename Cfg::R;
+    constexpr int N = Cfg::N, E = Cfg::E;
+    if constexpr (SEQ && LPT == 2) {
+        const LineSmem<R> l0[1] = {col_line<R, N, SLOTS>(sm, 0, id.slot)};
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            cpx<R> u[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) u[0][m] = v[l][m];
+            line_fft<R, N, E, INV, 1>(u, id.t, l0, tw, typename Cfg::Rads{});
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[l][m] = u[0][m];
+        }
+    } else {
+        LineSmem<R> ls[LPT];
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
+        line_fft<R, N, E, INV, LPT>(v, id.t, ls, tw, typename Cfg::Rads{});
+    }
+}
+// exchange buffers a column tile needs
+template <int LPT, bool SEQ> constexpr int col_buffers() { return SEQ && LPT == 2 ? 1 : 2; }
+
 // pass 1: pad + forward FFT along y.  W1 -> W2.
 template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p, int tile,
@@ -288,7 +320,7 @@ template <class R, int N, int SLOTS> constexpr int gsl_elems() {
     return (N + 1 + G - 1) / G * G * SLOTS;
 }
 
-template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
+template <class Cfg, int SLOTS, int LPT, bool CG, bool SEQ = false, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p, int tile,
                                             unsigned char* smem_raw, const In& in_src = In{},
                                             const Hook& after_load = Hook{}) {
@@ -304,7 +336,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     // start copying this column's octant row Ghat[kz][kyf][kx], kz <= N, to
     // shared memory (after the exchange buffers); it is needed only after
     // the forward transform
-    R* gsl = reinterpret_cast<R*>(sm + 2 * col_rows<R, N, SLOTS>() * SLOTS);
+    R* gsl = reinterpret_cast<R*>(sm + col_buffers<LPT, SEQ>() * col_rows<R, N, SLOTS>() * SLOTS);
     if (c.valid) {
         const int kys = c.other;
         const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
@@ -340,10 +372,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
             for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + id.t + T * m));
         }
     }
-    LineSmem<R> ls[LPT];
-#pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
-    line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
+    col_line_ffts<Cfg, SLOTS, LPT, SEQ, false>(v, id, sm, p.tw);
 
     // Green's multiply at frequency (kx, ky, kz), folded into the octant;
     // the column's octant row was copied to shared memory while the forward
@@ -375,7 +404,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
         }
     }
 
-    line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
+    col_line_ffts<Cfg, SLOTS, LPT, SEQ, true>(v, id, sm, p.tw);
 
     if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
 #pragma unroll
@@ -412,25 +441,7 @@ __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p,
                               : cpx<R>{0, 0};
     }
     after_load();
-    if constexpr (SEQ && LPT == 2) {
-        const LineSmem<R> l0[1] = {col_line<R, N, SLOTS>(sm, 0, id.slot)};
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-            cpx<R> u[1][E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) u[0][m] = v[l][m];
-            // the previous transform's last shared-memory read ended with a
-            // barrier, so this one may write the buffer at once
-            line_fft<R, N, E, true, 1>(u, id.t, l0, p.tw, typename Cfg::Rads{});
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[l][m] = u[0][m];
-        }
-    } else {
-        LineSmem<R> ls[LPT];
-#pragma unroll
-        for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
-        line_fft<R, N, E, true, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
-    }
+    col_line_ffts<Cfg, SLOTS, LPT, SEQ, true>(v, id, sm, p.tw);
 
     if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
         cpx<R>* dst = out + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
@@ -899,7 +910,7 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
             }
         };
         if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
-        else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
+        else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(p, tile, work, in, hook);
         else tile_y_inv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(p, tile, work, in, hook);
     }
 }
@@ -990,10 +1001,11 @@ template <int PASS, class Cfg, int S, int L, int MINB, int NBUF>
 cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, int n_wide, cudaStream_t st) {
     using B = TmaBox<PASS, Cfg, S, NBUF>;
     constexpr int NT = col_threads<Cfg, S, L>();
-    // (the single-buffered inverse y tile transforms its halves one after the
-    // other through one exchange buffer: half the work area)
-    constexpr size_t work = PASS == 2 ? col_smem_z<Cfg, S>()
-                                      : (PASS == 3 && NBUF == 1 && L == 2 ? col_smem<Cfg, S>() / 2 : col_smem<Cfg, S>());
+    // (the single-buffered z and inverse y tiles transform their halves one
+    // after the other through one exchange buffer)
+    constexpr bool SEQ = NBUF == 1 && L == 2 && PASS != 1;
+    constexpr size_t work = (SEQ ? col_smem<Cfg, S>() / 2 : col_smem<Cfg, S>()) +
+                            (PASS == 2 ? col_smem_z<Cfg, S>() - col_smem<Cfg, S>() : 0);
     constexpr size_t sm = B::WORK_OFF + work;
     // a tile whose buffers do not fit one CTA's shared memory, or whose box
     // would need more than 256 rows and several lines per box column, runs
