@@ -9,12 +9,15 @@
 // 2. Its M-point DFT per axis.  k is real and even in every axis, so the
 //    transform is real and even too and reduces to a DCT-I on the octant:
 //      K^(q) = sum_{d=0}^{n} c_d k(d) cos(pi q d / n),  c_0 = c_n = 1, else 2,
-//    applied along x, y, z as dense FP64 matrix products (a tiled DGEMM).
+//    applied along x, y, z by FP64 line FFTs (greens_dct.cu) for plans, and
+//    as dense FP64 matrix products (a tiled DGEMM) for the no-allocation
+//    solve's small grids.
 // 3. Scale by -G V / (Mx My Mz) (sign, cell volume and the inverse-FFT
 //    normalisation folded in) and store in the data-path precision.
+#include <algorithm>
 #include <cmath>
-#include <vector>
 
+#include "fft_core.cuh"
 #include "internal.h"
 
 namespace pgb {
@@ -156,20 +159,6 @@ __global__ void k_scale_store(const double* __restrict__ in, long long n, double
     }
 }
 
-// DCT-I matrix C[q][d] = c_d cos(pi q d / n), q, d in [0, n]; the angle is
-// reduced exactly in integers (q d mod 2n) before calling cos.
-static std::vector<double> dct1_matrix(int n) {
-    std::vector<double> c((size_t)(n + 1) * (n + 1));
-    const double pi = 3.14159265358979323846;
-    for (int q = 0; q <= n; ++q)
-        for (int d = 0; d <= n; ++d) {
-            const long long e = ((long long)q * d) % (2LL * n);
-            const double w = (d == 0 || d == n) ? 1.0 : 2.0;
-            c[(size_t)q * (n + 1) + d] = w * std::cos(pi * (double)e / (double)n);
-        }
-    return c;
-}
-
 #define PGB_TRY(x)                              \
     do {                                        \
         cudaError_t e_ = (x);                   \
@@ -190,60 +179,32 @@ cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz
                          const double* user_octant) {
     const int ex = nx + 1, ey = ny + 1, ez = nz + 1;
     const long long total = (long long)ex * ey * ez;
-    double *k0 = nullptr, *k1 = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
+    double *k0 = nullptr, *k1 = nullptr;
+    cpx<double>* tw[3] = {nullptr, nullptr, nullptr};
     cudaError_t err = cudaSuccess;
-    auto cleanup = [&]() {
-        cudaFree(k0);
-        cudaFree(k1);
-        cudaFree(cx);
-        cudaFree(cy);
-        cudaFree(cz);
-    };
     do {
         if ((err = cudaMalloc(&k0, total * sizeof(double))) != cudaSuccess) break;
         if ((err = cudaMalloc(&k1, total * sizeof(double))) != cudaSuccess) break;
-        const std::vector<double> hcx = dct1_matrix(nx), hcy = dct1_matrix(ny), hcz = dct1_matrix(nz);
-        if ((err = cudaMalloc(&cx, hcx.size() * sizeof(double))) != cudaSuccess) break;
-        if ((err = cudaMalloc(&cy, hcy.size() * sizeof(double))) != cudaSuccess) break;
-        if ((err = cudaMalloc(&cz, hcz.size() * sizeof(double))) != cudaSuccess) break;
-        if ((err = cudaMemcpyAsync(cx, hcx.data(), hcx.size() * sizeof(double), cudaMemcpyHostToDevice, st))) break;
-        if ((err = cudaMemcpyAsync(cy, hcy.data(), hcy.size() * sizeof(double), cudaMemcpyHostToDevice, st))) break;
-        if ((err = cudaMemcpyAsync(cz, hcz.data(), hcz.size() * sizeof(double), cudaMemcpyHostToDevice, st))) break;
+        const int n[3] = {nx, ny, nz};
+        for (int a = 0; a < 3 && err == cudaSuccess; ++a)
+            err = cudaMalloc(&tw[a], dct1_twiddle_entries(n[a]) * sizeof(cpx<double>));
+        if (err != cudaSuccess) break;
         if (user_octant) {  // a caller's kernel octant (host memory) instead of the Green's kernel
             if ((err = cudaMemcpyAsync(k0, user_octant, total * sizeof(double), cudaMemcpyHostToDevice, st)))
                 break;
         } else if ((err = build_kernel_octant(nx, ny, nz, hx, hy, hz, r_near, k0, st))) {
             break;
         }
-
-        // x: k1[zy][q] = sum_d k0[zy][d] Cx[q][d]
-        GemmDesc g{};
-        g.A = k0; g.sAi = ex; g.sAl = 1;
-        g.B = cx; g.sBl = 1; g.sBj = ex;
-        g.D = k1; g.sDi = ex; g.sDj = 1;
-        g.I = ey * ez; g.J = ex; g.L = ex;
-        if ((err = dgemm(g, 1, st))) break;
-        // y: k0[z][q][x] = sum_d Cy[q][d] k1[z][d][x]
-        g = GemmDesc{};
-        g.A = cy; g.sAb = 0; g.sAi = ey; g.sAl = 1;
-        g.B = k1; g.sBb = (long long)ey * ex; g.sBl = ex; g.sBj = 1;
-        g.D = k0; g.sDb = (long long)ey * ex; g.sDi = ex; g.sDj = 1;
-        g.I = ey; g.J = ex; g.L = ey;
-        if ((err = dgemm(g, ez, st))) break;
-        // z: k1[q][yx] = sum_d Cz[q][d] k0[d][yx]
-        g = GemmDesc{};
-        g.A = cz; g.sAi = ez; g.sAl = 1;
-        g.B = k0; g.sBl = (long long)ey * ex; g.sBj = 1;
-        g.D = k1; g.sDi = (long long)ey * ex; g.sDj = 1;
-        g.I = ez; g.J = ey * ex; g.L = ez;
-        if ((err = dgemm(g, 1, st))) break;
-
+        if ((err = dct1_octant(k0, k1, tw, nx, ny, nz, st))) break;  // result in k1
         int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
         k_scale_store<<<blocks, 256, 0, st>>>(k1, total, scale, out_f32, out_f64);
         if ((err = cudaGetLastError())) break;
         err = cudaStreamSynchronize(st);
     } while (0);
-    cleanup();
+    if (err != cudaSuccess) cudaStreamSynchronize(st);  // no queued work may outlive the buffers
+    cudaFree(k0);
+    cudaFree(k1);
+    for (int a = 0; a < 3; ++a) cudaFree(tw[a]);
     return err;
 }
 

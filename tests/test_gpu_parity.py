@@ -51,8 +51,12 @@ def gpu_solve(pg, rho, h=1.0, G=1.0, precision="fp32", flags=0):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("shape,h", [((16, 16, 16), 1.0), ((32, 16, 48), (1.0, 0.5, 2.0)),
-                                      ((48, 32, 16), (0.7, 1.3, 0.9))])
+                                      ((48, 32, 16), (0.7, 1.3, 0.9)), ((16, 64, 96), (1.0, 0.8, 1.2)),
+                                      ((128, 192, 16), 1.0), ((256, 16, 32), (0.5, 1.0, 1.0)),
+                                      ((384, 16, 16), 1.0), ((512, 16, 16), (1.0, 1.0, 0.5))])
 def test_greens_octant_matches_oracle(pg, oracle_mod, shape, h):
+    # the plan's FP64 DCT-I (line FFTs of every supported length) against the
+    # oracle's full FFT of the wrapped kernel
     nz, ny, nx = shape
     ref = oracle_mod.greens_hat(shape, h=h, G=1.7).real[:nz + 1, :ny + 1, :nx + 1] / (8.0 * nx * ny * nz)
     with pg.Plan(nx, ny, nz, h=h, G=1.7, precision="fp64") as plan:
