@@ -17,7 +17,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "fft_core.cuh"
+#include "greens_dct.h"
 #include "internal.h"
 
 namespace pgb {

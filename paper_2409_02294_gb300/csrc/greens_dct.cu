@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "configs.cuh"
+#include "greens_dct.h"
 #include "internal.h"
 
 namespace pgb {

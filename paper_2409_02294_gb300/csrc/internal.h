@@ -35,14 +35,6 @@ cudaError_t build_kernel_octant(int nx, int ny, int nz, double hx, double hy, do
 bool z_tc_supported(int N);
 cudaError_t launch_z_tc(int N, bool bf16, const PassParams<float>& p, cudaStream_t st);
 
-// DCT-I of a k(d) octant along x, y and z by FP64 line FFTs (greens_dct.cu):
-// k holds the octant ((nx+1)(ny+1)(nz+1) doubles, x fastest) and is used as
-// scratch, the result is left in tmp (same size); tw[a] has room for
-// dct1_twiddle_entries(n_a) FP64 complex entries.  Queued on st.
-template <class R> struct cpx;
-size_t dct1_twiddle_entries(int n);
-cudaError_t dct1_octant(double* k, double* tmp, cpx<double>* const tw[3], int nx, int ny, int nz, cudaStream_t st);
-
 // DCT-I transform + scaling of a k(d) octant on caller-provided buffers
 // (no allocation, no synchronisation); see greens.cu.
 cudaError_t greens_transform_into(double* kbuf, double* tmp, const double* cx, const double* cy,
