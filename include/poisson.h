@@ -268,7 +268,7 @@ typedef struct {
     int r_near;
     unsigned flags;
     size_t workspace_bytes;  /* W1 + W2 complex work buffers */
-    size_t greens_bytes;     /* transformed Green's function octant */
+    size_t greens_bytes;     /* device bytes of the transformed Green's function octant (kx padded to 64 bytes) */
     long long row_stride;    /* complex elements per work-buffer row */
     int variant[5];          /* kernel variant in use per pass */
     int variant_count[5];    /* variants available per pass */

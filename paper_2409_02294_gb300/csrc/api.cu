@@ -384,6 +384,20 @@ cudaError_t plan_run_pass(const poisson_plan_s* pl, int pass, const void* rho, v
 int plan_default_variant(const poisson_plan_s* pl, int pass) { return default_variant(pl->prec, pass); }
 }  // namespace pgb
 
+// the octant in its device block layout (greens_layout.h), rearranged to
+// [kz][ky][kx] doubles on the host
+template <class R>
+static poisson_status copy_greens_t(const void* dev, int nx, int ny, int nz, double* host_out) {
+    std::vector<R> tmp((size_t)greens_elems<R>(nx, ny, nz));
+    cudaError_t e = cudaMemcpy(tmp.data(), dev, tmp.size() * sizeof(R), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int kz = 0; kz <= nz; ++kz)
+        for (int ky = 0; ky <= ny; ++ky)
+            for (int kx = 0; kx <= nx; ++kx)
+                host_out[((size_t)kz * (ny + 1) + ky) * (nx + 1) + kx] = tmp[greens_index<R>(kx, ky, kz, nx, nz)];
+    return POISSON_OK;
+}
+
 extern "C" {
 
 const char* poisson_status_string(poisson_status s) {
@@ -461,7 +475,8 @@ poisson_status create_plan(poisson_plan_t* out, int nx, int ny, int nz, double h
     cudaError_t e;
     const size_t w1 = (size_t)nz * ny * p->sx * p->csize;
     const size_t w2 = (size_t)nz * 2 * ny * p->sx * p->csize;
-    const size_t gb = (size_t)(nx + 1) * (ny + 1) * (nz + 1) * p->rsize;
+    const size_t gb = prec == POISSON_FP64 ? (size_t)greens_elems<double>(nx, ny, nz) * sizeof(double)
+                                           : (size_t)greens_elems<float>(nx, ny, nz) * sizeof(float);
     if ((e = cudaMalloc(&p->w1, w1)) != cudaSuccess ||
         (e = cudaMalloc(&p->w2, w2)) != cudaSuccess ||
         (e = cudaMalloc(&p->greens, gb)) != cudaSuccess ||
@@ -652,7 +667,9 @@ poisson_status poisson_plan_get_info(poisson_plan_t plan, poisson_plan_info* inf
     info->r_near = plan->r_near;
     info->flags = plan->flags;
     info->workspace_bytes = (size_t)plan->nz * 3 * plan->ny * plan->sx * plan->csize;
-    info->greens_bytes = (size_t)(plan->nx + 1) * (plan->ny + 1) * (plan->nz + 1) * plan->rsize;
+    info->greens_bytes = plan->prec == POISSON_FP64
+                             ? (size_t)greens_elems<double>(plan->nx, plan->ny, plan->nz) * sizeof(double)
+                             : (size_t)greens_elems<float>(plan->nx, plan->ny, plan->nz) * sizeof(float);
     info->row_stride = plan->sx;
     for (int pass = 0; pass < 5; ++pass) {
         info->variant[pass] = plan->var[pass];
@@ -690,15 +707,11 @@ poisson_status poisson_plan_set_variant(poisson_plan_t plan, int pass, int varia
 
 poisson_status poisson_plan_copy_greens(poisson_plan_t plan, double* host_out, size_t count) {
     if (!plan || !host_out) return POISSON_ERR_ARG;
-    const size_t n = (size_t)(plan->nx + 1) * (plan->ny + 1) * (plan->nz + 1);
-    if (count < n) return POISSON_ERR_ARG;
-    if (plan->prec == POISSON_FP64)
-        return cuda_status(cudaMemcpy(host_out, plan->greens, n * sizeof(double), cudaMemcpyDeviceToHost));
-    std::vector<float> tmp(n);
-    cudaError_t e = cudaMemcpy(tmp.data(), plan->greens, n * sizeof(float), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_status(e);
-    for (size_t i = 0; i < n; ++i) host_out[i] = tmp[i];
-    return POISSON_OK;
+    const int nx = plan->nx, ny = plan->ny, nz = plan->nz;
+    if (count < (size_t)(nx + 1) * (ny + 1) * (nz + 1)) return POISSON_ERR_ARG;
+    // the device block layout (greens_layout.h), rearranged on the host
+    if (plan->prec == POISSON_FP64) return copy_greens_t<double>(plan->greens, nx, ny, nz, host_out);
+    return copy_greens_t<float>(plan->greens, nx, ny, nz, host_out);
 }
 
 poisson_status poisson_plan_sync_status(poisson_plan_t plan, void* cuda_stream) {

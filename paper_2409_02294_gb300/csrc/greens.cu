@@ -18,6 +18,7 @@
 #include <cmath>
 
 #include "greens_dct.h"
+#include "greens_layout.h"
 #include "internal.h"
 
 namespace pgb {
@@ -149,14 +150,28 @@ static cudaError_t dgemm(const GemmDesc& g, int batch, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-__global__ void k_scale_store(const double* __restrict__ in, long long n, double s,
-                              float* __restrict__ of, double* __restrict__ od) {
+// Scale the dense octant in[kz][ky][kx] and store it in the block layout of
+// greens_layout.h (zeros beyond kx = nx), one output element per step.
+template <class R>
+__global__ void k_scale_store(const double* __restrict__ in, int nx, int ny, int nz, double s, R* __restrict__ out) {
+    constexpr int XW = greens_xw<R>();
+    const long long n = greens_elems<R>(nx, ny, nz), bands = greens_bands<R>(nx);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double v = s * in[i];
-        if (of) of[i] = (float)v;
-        else od[i] = v;
+        const long long r = i / XW, blk = r / (nz + 1);
+        const int kz = (int)(r - blk * (nz + 1)), ky = (int)(blk / bands);
+        const int kx = (int)(blk - ky * bands) * XW + (int)(i - r * XW);
+        out[i] = kx <= nx ? (R)(s * in[((long long)kz * (ny + 1) + ky) * (nx + 1) + kx]) : (R)0;
     }
+}
+
+static cudaError_t scale_store(const double* in, int nx, int ny, int nz, double s, float* of, double* od,
+                               cudaStream_t st) {
+    const long long n = of ? greens_elems<float>(nx, ny, nz) : greens_elems<double>(nx, ny, nz);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (of) k_scale_store<float><<<blocks, 256, 0, st>>>(in, nx, ny, nz, s, of);
+    else k_scale_store<double><<<blocks, 256, 0, st>>>(in, nx, ny, nz, s, od);
+    return cudaGetLastError();
 }
 
 #define PGB_TRY(x)                              \
@@ -196,9 +211,7 @@ cudaError_t build_greens(int nx, int ny, int nz, double hx, double hy, double hz
             break;
         }
         if ((err = dct1_octant(k0, k1, tw, nx, ny, nz, st))) break;  // result in k1
-        int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-        k_scale_store<<<blocks, 256, 0, st>>>(k1, total, scale, out_f32, out_f64);
-        if ((err = cudaGetLastError())) break;
+        if ((err = scale_store(k1, nx, ny, nz, scale, out_f32, out_f64, st))) break;
         err = cudaStreamSynchronize(st);
     } while (0);
     if (err != cudaSuccess) cudaStreamSynchronize(st);  // no queued work may outlive the buffers
@@ -216,12 +229,11 @@ namespace pgb {
 // buffers, with nothing allocated and nothing synchronised: kbuf holds the
 // k(d) octant on entry and is overwritten, tmp has the same size, cx/cy/cz
 // are the (n+1)^2 DCT-I matrices of the three axes, out receives the scaled
-// FP32 octant.  All work is queued on st.
+// FP32 octant (block layout of greens_layout.h).  All work is queued on st.
 cudaError_t greens_transform_into(double* kbuf, double* tmp, const double* cx, const double* cy,
                                   const double* cz, int nx, int ny, int nz, double scale,
                                   float* out, cudaStream_t st) {
     const int ex = nx + 1, ey = ny + 1, ez = nz + 1;
-    const long long total = (long long)ex * ey * ez;
     GemmDesc g{};
     g.A = kbuf; g.sAi = ex; g.sAl = 1;
     g.B = cx; g.sBl = 1; g.sBj = ex;
@@ -240,9 +252,7 @@ cudaError_t greens_transform_into(double* kbuf, double* tmp, const double* cx, c
     g.D = tmp; g.sDi = (long long)ey * ex; g.sDj = 1;
     g.I = ez; g.J = ey * ex; g.L = ez;
     PGB_TRY(dgemm(g, 1, st));
-    int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-    k_scale_store<<<blocks, 256, 0, st>>>(tmp, total, scale, out, nullptr);
-    return cudaGetLastError();
+    return scale_store(tmp, nx, ny, nz, scale, out, nullptr, st);
 }
 
 }  // namespace pgb

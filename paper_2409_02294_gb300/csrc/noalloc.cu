@@ -81,9 +81,9 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Byte offsets of every buffer inside the scratch array for one grid.
 struct Layout {
     size_t tw[3];      // axis twiddle tables (float2): W_2n^j, then the stage tables
-    size_t dct[3];     // (n+1)^2 DCT-I matrices (double), one per axis
-    size_t ghat;       // (nx+1)(ny+1)(nz+1) floats
-    size_t work;       // union of {k octant, tmp} (double) and {W1, W2} (float2)
+    size_t ghat;       // greens_elems<float>(nx, ny, nz) floats (block layout)
+    size_t work;       // union of {k octant, tmp, DCT-I matrices} (double) and {W1, W2} (float2)
+    size_t dct[3];     // (n+1)^2 DCT-I matrices (double), one per axis, inside the work region
     size_t w2;         // offset of W2 inside the work region
     size_t ktmp;       // offset of the second k buffer inside the work region
     size_t total;
@@ -98,20 +98,23 @@ Layout make_layout(int nx, int ny, int nz) {
         L.tw[a] = off;
         off += align256((size_t)pgb::axis_tw_list<float>(n[a], a == 0).total * sizeof(float2));
     }
-    for (int a = 0; a < 3; ++a) {
-        L.dct[a] = off;
-        off += align256((size_t)(n[a] + 1) * (n[a] + 1) * sizeof(double));
-    }
     const size_t oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
     L.ghat = off;
-    off += align256(oct * sizeof(float));
+    off += align256((size_t)pgb::greens_elems<float>(nx, ny, nz) * sizeof(float));
     L.sx = ((long long)(nx + 1) + 15) / 16 * 16;
     const size_t w1 = (size_t)nz * ny * L.sx * sizeof(float2);
     const size_t kb = align256(oct * sizeof(double));
     L.work = off;
     L.w2 = align256(w1);
     L.ktmp = kb;
-    const size_t work = std::max(L.w2 + 2 * w1, 2 * kb);
+    // the DCT-I matrices are needed only while the Green's function is
+    // built, before W1/W2 are written
+    size_t build = 2 * kb;
+    for (int a = 0; a < 3; ++a) {
+        L.dct[a] = off + build;
+        build += align256((size_t)(n[a] + 1) * (n[a] + 1) * sizeof(double));
+    }
+    const size_t work = std::max(L.w2 + 2 * w1, build);
     L.total = off + align256(work);
     return L;
 }

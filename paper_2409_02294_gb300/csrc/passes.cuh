@@ -16,13 +16,15 @@
 // Layout (complex elements, x fastest):
 //   W1[z][y][kx]        z < nz, y < ny,  kx <= nx   row stride sx
 //   W2[z][q*ny + k][kx] z < nz, q in {0,1} parity of ky = 2k + q, row stride sx
-//   Ghat[kz][ky][kx]    octant (nz+1)(ny+1)(nx+1) of the real, even transformed
-//                       Green's function, scaled by -G V / (Mx My Mz)
+//   Ghat(kx, ky, kz)    octant (nz+1)(ny+1)(nx+1) of the real, even transformed
+//                       Green's function, scaled by -G V / (Mx My Mz), in
+//                       blocks of 64 bytes of kx by all kz (greens_layout.h)
 #pragma once
 
 #include <cstdlib>
 
 #include "fft_core.cuh"
+#include "greens_layout.h"
 #include "tma.cuh"
 
 namespace pgb {
@@ -341,8 +343,8 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
         const int kys = c.other;
         const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
         const int kyf = ky <= ny ? ky : 2 * ny - ky;
-        const long long gz = (long long)(ny + 1) * (nx + 1);
-        const R* g = p.greens + (long long)kyf * (nx + 1) + c.kx;
+        constexpr int gz = greens_xw<R>();  // kz stride within the block
+        const R* g = p.greens + greens_base<R>(c.kx, kyf, nx, p.nz);
         constexpr int TPS = (LPT == 1 ? 2 : 1) * T;  // threads per slot
         const int u = id.t + (LPT == 1 ? id.q * T : 0);
         if constexpr (TPS % gsl_group<R, SLOTS>() == 0) {

@@ -78,8 +78,8 @@ __device__ __forceinline__ void tile_z_conv_pk(const PassParams<float>& p, int t
         const int kys = c.other;
         const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
         const int kyf = ky <= ny ? ky : 2 * ny - ky;
-        const long long gz = (long long)(ny + 1) * (nx + 1);
-        const R* g = p.greens + (long long)kyf * (nx + 1) + c.kx;
+        constexpr int gz = greens_xw<R>();  // kz stride within the block
+        const R* g = p.greens + greens_base<R>(c.kx, kyf, nx, p.nz);
         const int u = id.t;
         if constexpr (T % gsl_group<R, SLOTS>() == 0) {
             R* sp = gsl + gsl_idx<R, SLOTS>(u, id.slot);

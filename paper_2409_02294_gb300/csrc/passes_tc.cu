@@ -41,15 +41,17 @@ __device__ __forceinline__ void tile_z_conv_tc(const PassParams<float>& p, int t
         const int kys = ce.other;
         const int ky = kys < ny ? 2 * kys : 2 * (kys - ny) + 1;
         const int kyf = ky <= ny ? ky : 2 * ny - ky;
-        s_goff[tid] = ce.valid ? (long long)kyf * (nx + 1) + ce.kx : -1LL;
+        s_goff[tid] = ce.valid ? greens_base<R>(ce.kx, kyf, nx, p.nz) : -1LL;
     }
     __syncthreads();
     {
-        const long long gz = (long long)(ny + 1) * (nx + 1);
+        // columns fastest across threads: a warp reads four kz rows of the
+        // tile's 8 columns (32 contiguous bytes each in the block layout)
+        constexpr int gz = greens_xw<R>();
         for (int i = tid; i < SLOTS * (N + 1); i += 256) {
-            const int s = i / (N + 1), kz = i - s * (N + 1);
+            const int kz = i / SLOTS, s = i - kz * SLOTS;
             const long long off = s_goff[s];
-            gsl[i] = off >= 0 ? __ldg(p.greens + kz * gz + off) : (R)0;
+            gsl[s * (N + 1) + kz] = off >= 0 ? __ldg(p.greens + kz * gz + off) : (R)0;
         }
     }
     // 1. load x[t + 16 r]; the odd half is pre-twiddled by W_2N^j

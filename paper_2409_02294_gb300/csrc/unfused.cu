@@ -74,7 +74,7 @@ __global__ void k_unf_mul(cpx<float>* __restrict__ P, const float* __restrict__ 
         const long long r = i / Mx;
         const int ky = (int)(r % My), kz = (int)(r / My);
         const int fx = min(kx, Mx - kx), fy = min(ky, My - ky), fz = min(kz, Mz - kz);
-        P[i] = scale(P[i], g[((long long)fz * (ny + 1) + fy) * (nx + 1) + fx]);
+        P[i] = scale(P[i], g[greens_index<float>(fx, fy, fz, nx, Mz / 2)]);
     }
 }
 
