@@ -85,6 +85,7 @@ def pass_bytes(nx, ny, nz, rsize=4):  # rsize: bytes per real value
 # the sources the pass kernels (five passes, tensor-core z pass) are built
 # from: a profile's counters stay valid while these are unchanged
 KERNEL_SOURCES = ("fft_core.cuh", "fft_pk.cuh", "passes.cuh", "passes_pk.cuh", "configs.cuh", "tma.cuh", "tc_dft.cuh", "internal.h",
+                  "greens_layout.h",
                   "twiddles.cu", "passes_f32_row.cu", "passes_f32_y.cu", "passes_f32_z.cu", "passes_f64.cu",
                   "passes_tc.cu")
 

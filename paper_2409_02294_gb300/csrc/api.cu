@@ -264,9 +264,12 @@ poisson_status autotune(poisson_plan_s* pl, cudaStream_t st) {
                     if (rep >= 1) best[mode] = ms < best[mode] ? ms : best[mode];
                 }
             }
+            // another mode replaces the five launches only when it is
+            // clearly faster: these timings run on zero inputs with a warm
+            // L2, where differences of a percent do not carry over
             int bm = 0;
             for (int mode = 1; mode < 5; ++mode)
-                if (best[mode] < best[bm]) bm = mode;
+                if (best[mode] < 0.98f * best[0] && best[mode] < best[bm]) bm = mode;
             pl->use_fused = bm;
         }
     } while (0);

@@ -166,6 +166,70 @@ __device__ __forceinline__ void sfor_impl(F&& f) {
 template <int N, class F> __device__ __forceinline__ void sfor(F&& f) { sfor_impl<0, N>(f); }
 
 // --------------------------------------------------------------------------
+// compile-time cos and sin of pi p / q: the angle is reduced exactly (in
+// integers) to a quarter turn plus phi in [0, pi/2), phi or pi/2 - phi
+// (whichever is <= pi/4) goes through the Taylor series, summed to far below
+// double rounding, and the quarter turns rotate the result
+// --------------------------------------------------------------------------
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 12; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k <= 12; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+struct CosSin {
+    double c, s;
+};
+__host__ __device__ constexpr CosSin cos_sin_pi_frac(long long p, long long q) {
+    const long long P = ((p % (2 * q)) + 2 * q) % (2 * q);  // angle pi P / q in [0, 2 pi)
+    const long long k = (2 * P) / q;                          // quarter turns
+    const long long r = 2 * P - k * q;                        // phi = pi r / (2 q) in [0, pi/2)
+    const double half_pi_over_q = 1.57079632679489661923132169163975144 / (double)q;
+    double c = 0.0, s = 0.0;
+    if (2 * r <= q) {
+        c = taylor_cos(half_pi_over_q * (double)r);
+        s = taylor_sin(half_pi_over_q * (double)r);
+    } else {
+        c = taylor_sin(half_pi_over_q * (double)(q - r));
+        s = taylor_cos(half_pi_over_q * (double)(q - r));
+    }
+    if (k == 0) return {c, s};
+    if (k == 1) return {-s, c};
+    if (k == 2) return {-c, -s};
+    return {s, -c};
+}
+
+// The pre- and post-multiplies of a padded (length 2N) transform use
+// W_2N^j at j = t + T m, m < E (T = N / E).  They factor as W_2N^t, one
+// table load per thread, times W_2E^m = exp(-i pi m / E), a constant of the
+// unrolled loop, instead of one table load per element.
+template <int N, int E, class R> struct LineRamp {
+    cpx<R> wt;
+    __device__ __forceinline__ LineRamp(const cpx<R>* tw2N, int t) : wt(ldg_c(tw2N + t)) {}
+    template <int M> __device__ __forceinline__ cpx<R> at() const {
+        if constexpr (M == 0) {
+            return wt;
+        } else if constexpr (2 * M == E) {  // W_2E^(E/2) = -i
+            return mul_mi(wt);
+        } else {
+            constexpr CosSin w = cos_sin_pi_frac(M, E);
+            constexpr R c = (R)w.c, s = (R)(-w.s);
+            return {wt.x * c - wt.y * s, wt.x * s + wt.y * c};
+        }
+    }
+};
+
+// --------------------------------------------------------------------------
 // in-register DFTs, natural order in and out: a[k] <- sum_n a[n] W_R^{nk}
 // --------------------------------------------------------------------------
 template <int R_, bool INV, class R> struct Dft;

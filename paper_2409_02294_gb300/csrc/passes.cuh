@@ -242,8 +242,11 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + id.t + T * m));
+            const LineRamp<N, E, R> rw(p.tw, id.t);
+            sfor<E>([&](auto m_) {
+                constexpr int m = decltype(m_)::value;
+                v[l][m] = cmul(v[0][m], rw.template at<m>());
+            });
         }
     }
     LineSmem<R> ls[LPT];
@@ -272,18 +275,20 @@ __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cf
                                                const cpx<typename Cfg::R>* tw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
+    const LineRamp<N, E, R> rw(tw, id.t);
     if constexpr (LPT == 2) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + cmulc(v[1][m], ldg_c(tw + id.t + T * m));
+        sfor<E>([&](auto m_) {
+            constexpr int m = decltype(m_)::value;
+            v[0][m] = v[0][m] + cmulc(v[1][m], rw.template at<m>());
+        });
         return true;
     } else {
         const LineSmem<R> lodd = col_line<R, N, SLOTS>(sm, 1, id.slot);
         if (id.q) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int j = id.t + T * m;
-                lodd[j] = cmulc(v[0][m], ldg_c(tw + j));
-            }
+            sfor<E>([&](auto m_) {
+                constexpr int m = decltype(m_)::value;
+                lodd[id.t + T * m] = cmulc(v[0][m], rw.template at<m>());
+            });
         }
         __syncthreads();
         if (!id.q) {
@@ -370,8 +375,11 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + id.t + T * m));
+            const LineRamp<N, E, R> rw(p.tw, id.t);
+            sfor<E>([&](auto m_) {
+                constexpr int m = decltype(m_)::value;
+                v[l][m] = cmul(v[0][m], rw.template at<m>());
+            });
         }
     }
     col_line_ffts<Cfg, SLOTS, LPT, SEQ, false>(v, id, sm, p.tw);
@@ -556,8 +564,11 @@ __device__ __forceinline__ void tile_x_fwd(const PassParams<typename Cfg::R>& p,
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[l][m] = cmul(v[0][m], ldg_c(p.tw + t + T * m));
+            const LineRamp<N, E, R> rw(p.tw, t);
+            sfor<E>([&](auto m_) {
+                constexpr int m = decltype(m_)::value;
+                v[l][m] = cmul(v[0][m], rw.template at<m>());
+            });
         }
     }
     LineSmem<R> ls[LPT];
@@ -666,14 +677,15 @@ __device__ __forceinline__ void tile_x_inv_direct(const PassParams<typename Cfg:
     R* oa = static_cast<R*>(p.out) + (long long)(r0 + 2 * pr) * N;
     R* ob = oa + N;
     bool bad = false;
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
+    const LineRamp<N, E, R> rw(p.tw, t);
+    sfor<E>([&](auto m_) {
+        constexpr int m = decltype(m_)::value;
         const int j = t + T * m;
-        const cpx<R> x = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + j));
+        const cpx<R> x = v[0][m] + cmulc(v[1][m], rw.template at<m>());
         if (has_a) oa[j] = x.x;
         if (has_b) ob[j] = x.y;
         bad |= (has_a && not_finite(x.x)) || (has_b && not_finite(x.y));
-    }
+    });
     if (p.check_finite) flag_non_finite(p.status, bad);
 }
 
@@ -747,17 +759,19 @@ __device__ __forceinline__ void tile_x_inv(const PassParams<typename Cfg::R>& p,
 
     // z[j] = a[j] + W_2N^-j b[j]
     bool holder = true;
+    const LineRamp<N, E, R> rw(p.tw, t);
     if constexpr (LPT == 2) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + cmulc(v[1][m], ldg_c(p.tw + t + T * m));
+        sfor<E>([&](auto m_) {
+            constexpr int m = decltype(m_)::value;
+            v[0][m] = v[0][m] + cmulc(v[1][m], rw.template at<m>());
+        });
     } else {
         const LineSmem<R> lodd = {sm + row_line_off<Cfg, PAIRS>(1, pr), 1, SH, 1};
         if (id.q) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int j = t + T * m;
-                lodd[j] = cmulc(v[0][m], ldg_c(p.tw + j));
-            }
+            sfor<E>([&](auto m_) {
+                constexpr int m = decltype(m_)::value;
+                lodd[t + T * m] = cmulc(v[0][m], rw.template at<m>());
+            });
         }
         __syncthreads();
         if (!id.q) {
