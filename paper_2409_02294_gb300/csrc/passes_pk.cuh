@@ -41,11 +41,12 @@ __device__ __forceinline__ void tile_y_fwd_pk(const PassParams<float>& p, int ti
 
     c2 v[E];
     const cpx<float>* src = in + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
+    const LineRamp<N, E, float> rw(p.tw, id.t);
+    sfor<E>([&](auto m_) {
+        constexpr int m = decltype(m_)::value;
         const cpx<float> x = c.valid ? src[(long long)(T * m) * sx] : cpx<float>{0, 0};
-        v[m] = pack_even_odd(x, ldg_c(p.tw + id.t + T * m));
-    }
+        v[m] = pack_even_odd(x, rw.template at<m>());
+    });
     const LineSmemPk ls{reinterpret_cast<float4*>(smem_raw) + id.slot, SLOTS, 30, 0};
     line_fft_pk<N, E, false>(v, id.t, ls, p.tw, typename Cfg::Rads{});
     if (c.valid) {
@@ -95,12 +96,12 @@ __device__ __forceinline__ void tile_z_conv_pk(const PassParams<float>& p, int t
 
     c2 v[E];
     cpx<R>* col = w + (long long)c.other * p.sx + c.kx;
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int j = id.t + T * m;
-        const cpx<R> x = c.valid ? col[(long long)j * plane] : cpx<R>{0, 0};
-        v[m] = pack_even_odd(x, ldg_c(p.tw + j));
-    }
+    const LineRamp<N, E, R> rw(p.tw, id.t);
+    sfor<E>([&](auto m_) {
+        constexpr int m = decltype(m_)::value;
+        const cpx<R> x = c.valid ? col[(long long)(id.t + T * m) * plane] : cpx<R>{0, 0};
+        v[m] = pack_even_odd(x, rw.template at<m>());
+    });
     const LineSmemPk ls{smp + id.slot, SLOTS, 30, 0};
     line_fft_pk<N, E, false>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
@@ -135,11 +136,10 @@ __device__ __forceinline__ void tile_z_conv_pk(const PassParams<float>& p, int t
 
     // x[j] = a[j] + W_2N^-j b[j], j < N
     if (c.valid) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int j = id.t + T * m;
-            col[(long long)j * plane] = c2_a(v[m]) + cmulc(c2_b(v[m]), ldg_c(p.tw + j));
-        }
+        sfor<E>([&](auto m_) {
+            constexpr int m = decltype(m_)::value;
+            col[(long long)(id.t + T * m) * plane] = c2_a(v[m]) + cmulc(c2_b(v[m]), rw.template at<m>());
+        });
     }
 }
 
@@ -170,9 +170,11 @@ __device__ __forceinline__ void tile_y_inv_pk(const PassParams<float>& p, int ti
     line_fft_pk<N, E, true>(v, id.t, ls, p.tw, typename Cfg::Rads{});
     if (c.valid) {
         cpx<float>* dst = out + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
-#pragma unroll
-        for (int m = 0; m < E; ++m)
-            dst[(long long)(T * m) * sx] = c2_a(v[m]) + cmulc(c2_b(v[m]), ldg_c(p.tw + id.t + T * m));
+        const LineRamp<N, E, float> rw(p.tw, id.t);
+        sfor<E>([&](auto m_) {
+            constexpr int m = decltype(m_)::value;
+            dst[(long long)(T * m) * sx] = c2_a(v[m]) + cmulc(c2_b(v[m]), rw.template at<m>());
+        });
     }
 }
 
