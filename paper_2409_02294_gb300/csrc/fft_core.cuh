@@ -34,6 +34,8 @@ template <class R> __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> 
 template <class R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.x - b.x, a.y - b.y}; }
 template <class R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a) { return {-a.x, -a.y}; }
 template <class R> __device__ __forceinline__ cpx<R> scale(cpx<R> a, R s) { return {a.x * s, a.y * s}; }
+// conj(a) * s
+template <class R> __device__ __forceinline__ cpx<R> scale_conj(cpx<R> a, R s) { return {a.x * s, a.y * -s}; }
 // a * b
 template <class R> __device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};

@@ -266,9 +266,11 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
 }
 
 // Final combine of the cropped inverse, x[j] = a[j] + W_2N^-j b[j] with a,b
-// the inverse transforms of the even and odd halves.  Returns true in the
-// threads that hold x[t + T m] in v[0][m] afterwards.
-template <class Cfg, int SLOTS, int LPT>
+// the inverse transforms of the even and odd halves.  CONJ: the halves hold
+// conj(a) and conj(b) (an inverse run as a conjugated forward transform),
+// and x = conj(conj(a) + W_2N^j conj(b)).  Returns true in the threads that
+// hold x[t + T m] in v[0][m] afterwards.
+template <class Cfg, int SLOTS, int LPT, bool CONJ = false>
 __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cfg::E],
                                                const ColIds<Cfg, SLOTS, LPT>& id,
                                                cpx<typename Cfg::R>* sm,
@@ -279,7 +281,12 @@ __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cf
     if constexpr (LPT == 2) {
         sfor<E>([&](auto m_) {
             constexpr int m = decltype(m_)::value;
-            v[0][m] = v[0][m] + cmulc(v[1][m], rw.template at<m>());
+            if constexpr (CONJ) {
+                const cpx<R> s = v[0][m] + cmul(v[1][m], rw.template at<m>());
+                v[0][m] = {s.x, -s.y};
+            } else {
+                v[0][m] = v[0][m] + cmulc(v[1][m], rw.template at<m>());
+            }
         });
         return true;
     } else {
@@ -287,13 +294,16 @@ __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cf
         if (id.q) {
             sfor<E>([&](auto m_) {
                 constexpr int m = decltype(m_)::value;
-                lodd[id.t + T * m] = cmulc(v[0][m], rw.template at<m>());
+                lodd[id.t + T * m] = CONJ ? cmul(v[0][m], rw.template at<m>()) : cmulc(v[0][m], rw.template at<m>());
             });
         }
         __syncthreads();
         if (!id.q) {
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[0][m] = v[0][m] + lodd[id.t + T * m];
+            for (int m = 0; m < E; ++m) {
+                const cpx<R> s = v[0][m] + lodd[id.t + T * m];
+                v[0][m] = CONJ ? cpx<R>{s.x, -s.y} : s;
+            }
         }
         return id.q == 0;
     }
@@ -382,41 +392,48 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
             });
         }
     }
-    col_line_ffts<Cfg, SLOTS, LPT, SEQ, false>(v, id, sm, p.tw);
+    // The inverse transform runs as conj(FFT(conj(.))) through the forward
+    // transform's code: a two-trip loop that is not unrolled, so the tile
+    // holds one copy of the line transforms (half the instruction footprint
+    // of a forward and an inverse copy).  The Green's multiply conjugates its
+    // products and the combine conjugates back.
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
+        col_line_ffts<Cfg, SLOTS, LPT, SEQ, false>(v, id, sm, p.tw);
+        if (ph == 1) break;
 
-    // Green's multiply at frequency (kx, ky, kz), folded into the octant;
-    // the column's octant row was copied to shared memory while the forward
-    // transform ran.  kz = 2 (t + T m) + q is <= N exactly for m < E/2.
-    cp_async_commit_wait_all();
-    __syncthreads();
-    if (c.valid) {
+        // Green's multiply at frequency (kx, ky, kz), folded into the octant;
+        // the column's octant row was copied to shared memory while the forward
+        // transform ran.  kz = 2 (t + T m) + q is <= N exactly for m < E/2.
+        cp_async_commit_wait_all();
+        __syncthreads();
+        if (c.valid) {
 #pragma unroll
-        for (int l = 0; l < LPT; ++l) {
-            const int kz0 = 2 * id.t + id.half(l);
-            if constexpr (T % gsl_group<R, SLOTS>() == 0) {
-                // kz0 + 2 T m and 2N - kz0 - 2 T m keep the place of kz0 and
-                // 2N - kz0 within their blocks of G rows: constant offsets
-                // from two bases (the second base, beyond row N for small
-                // kz0, is only read back at rows <= N)
-                const int i_lo = gsl_idx<R, SLOTS>(kz0, id.slot);
-                const int i_hi = gsl_idx<R, SLOTS>(2 * N - kz0, id.slot);
+            for (int l = 0; l < LPT; ++l) {
+                const int kz0 = 2 * id.t + id.half(l);
+                if constexpr (T % gsl_group<R, SLOTS>() == 0) {
+                    // kz0 + 2 T m and 2N - kz0 - 2 T m keep the place of kz0 and
+                    // 2N - kz0 within their blocks of G rows: constant offsets
+                    // from two bases (the second base, beyond row N for small
+                    // kz0, is only read back at rows <= N)
+                    const int i_lo = gsl_idx<R, SLOTS>(kz0, id.slot);
+                    const int i_hi = gsl_idx<R, SLOTS>(2 * N - kz0, id.slot);
 #pragma unroll
-                for (int m = 0; m < E; ++m)
-                    v[l][m] = scale(v[l][m], gsl[m < E / 2 ? i_lo + 2 * T * m * SLOTS : i_hi - 2 * T * m * SLOTS]);
-            } else {
+                    for (int m = 0; m < E; ++m)
+                        v[l][m] = scale_conj(v[l][m], gsl[m < E / 2 ? i_lo + 2 * T * m * SLOTS : i_hi - 2 * T * m * SLOTS]);
+                } else {
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int kz = kz0 + 2 * T * m;
-                    const int kzf = (m < E / 2) ? kz : 2 * N - kz;
-                    v[l][m] = scale(v[l][m], gsl[gsl_idx<R, SLOTS>(kzf, id.slot)]);
+                    for (int m = 0; m < E; ++m) {
+                        const int kz = kz0 + 2 * T * m;
+                        const int kzf = (m < E / 2) ? kz : 2 * N - kz;
+                        v[l][m] = scale_conj(v[l][m], gsl[gsl_idx<R, SLOTS>(kzf, id.slot)]);
+                    }
                 }
             }
         }
     }
 
-    col_line_ffts<Cfg, SLOTS, LPT, SEQ, true>(v, id, sm, p.tw);
-
-    if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
+    if (combine_halves<Cfg, SLOTS, LPT, true>(v, id, sm, p.tw) && c.valid) {
 #pragma unroll
         for (int m = 0; m < E; ++m) col[(long long)(id.t + T * m) * plane] = v[0][m];
     }
