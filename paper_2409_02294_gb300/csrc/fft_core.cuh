@@ -75,6 +75,27 @@ template <class R> __device__ __forceinline__ void ldg_c2(const cpx<R>* p, cpx<R
     }
 }
 
+// Twiddle-table reads: from global memory through the read-only path, or
+// (SM) from a copy of the table in shared memory (the persistent column
+// kernels keep one per CTA: their tiles fill most of the unified L1/shared
+// storage, and table reads through the small L1 that remains mostly miss).
+template <bool SM, class R> __device__ __forceinline__ cpx<R> tw_ld(const cpx<R>* p) {
+    if constexpr (SM) return *p;
+    else return ldg_c(p);
+}
+template <bool SM, class R> __device__ __forceinline__ void tw_ld2(const cpx<R>* p, cpx<R>& a, cpx<R>& b) {
+    if constexpr (SM && std::is_same<R, float>::value) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a = {v.x, v.y};
+        b = {v.z, v.w};
+    } else if constexpr (SM) {
+        a = p[0];
+        b = p[1];
+    } else {
+        ldg_c2(p, a, b);
+    }
+}
+
 // Load of data that this kernel launch may also have written elsewhere on
 // the GPU: CG = true bypasses L1 (ld.global.cg), which is required when a
 // persistent kernel reads data produced by other SMs in the same launch.
@@ -215,9 +236,9 @@ __host__ __device__ constexpr CosSin cos_sin_pi_frac(long long p, long long q) {
 // W_2N^j at j = t + T m, m < E (T = N / E).  They factor as W_2N^t, one
 // table load per thread, times W_2E^m = exp(-i pi m / E), a constant of the
 // unrolled loop, instead of one table load per element.
-template <int N, int E, class R> struct LineRamp {
+template <int N, int E, class R, bool TWS = false> struct LineRamp {
     cpx<R> wt;
-    __device__ __forceinline__ LineRamp(const cpx<R>* tw2N, int t) : wt(ldg_c(tw2N + t)) {}
+    __device__ __forceinline__ LineRamp(const cpx<R>* tw2N, int t) : wt(tw_ld<TWS>(tw2N + t)) {}
     template <int M> __device__ __forceinline__ cpx<R> at() const {
         if constexpr (M == 0) {
             return wt;
@@ -390,7 +411,7 @@ template <class R> struct LineSmem {
 // to give the scheduler independent work.  v[l][m] = x_l[t + T*m].
 // tw2N: an axis twiddle table (W_{2N}^j, j < 2N, then the stage tables);
 // TOFF: offset of this stage's table.
-template <class R, int N, int E, bool INV, int NL, int NS, int TOFF, int RAD, int... REST>
+template <class R, int N, int E, bool INV, int NL, bool TWS, int NS, int TOFF, int RAD, int... REST>
 __device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSmem<R> (&sm)[NL],
                                          const cpx<R>* __restrict__ tw2N) {
     constexpr int T = N / E;
@@ -407,7 +428,7 @@ __device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSm
             k = b % NS;
             const cpx<R>* st = tw2N + TOFF;
             if constexpr (RAD == 2) {
-                const cpx<R> w = ldg_c(st + k);
+                const cpx<R> w = tw_ld<TWS>(st + k);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) v[l][g + B] = cmul_dir<INV>(v[l][g + B], w);
             } else {
@@ -415,8 +436,8 @@ __device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSm
                 for (int q = 0; q < RAD / 2; ++q) {
                     const int r0 = 2 * q + 1;
                     cpx<R> w0, w1;
-                    if (r0 + 1 < RAD) ldg_c2(st + 2 * (q * NS + k), w0, w1);
-                    else w0 = ldg_c(st + 2 * (q * NS + k));
+                    if (r0 + 1 < RAD) tw_ld2<TWS>(st + 2 * (q * NS + k), w0, w1);
+                    else w0 = tw_ld<TWS>(st + 2 * (q * NS + k));
 #pragma unroll
                     for (int l = 0; l < NL; ++l) {
                         v[l][g + B * r0] = cmul_dir<INV>(v[l][g + B * r0], w0);
@@ -448,15 +469,16 @@ __device__ __forceinline__ void stockham(cpx<R> (&v)[NL][E], int t, const LineSm
 #pragma unroll
             for (int m = 0; m < E; ++m) v[l][m] = sm[l][t + T * m];
         __syncthreads();
-        stockham<R, N, E, INV, NL, NS * RAD, TOFF + stage_tw_size<NS, RAD>(), REST...>(v, t, sm, tw2N);
+        stockham<R, N, E, INV, NL, TWS, NS * RAD, TOFF + stage_tw_size<NS, RAD>(), REST...>(v, t, sm, tw2N);
     }
 }
 
-template <class R, int N, int E, bool INV, int NL, int... Rs>
+// TWS: tw2N points to a copy of the table in shared memory
+template <class R, int N, int E, bool INV, int NL, bool TWS = false, int... Rs>
 __device__ __forceinline__ void line_fft(cpx<R> (&v)[NL][E], int t, const LineSmem<R> (&sm)[NL],
                                          const cpx<R>* __restrict__ tw2N, Radices<Rs...>) {
     static_assert(RadProd<Rs...>::v == N, "radices must multiply to N");
-    stockham<R, N, E, INV, NL, 1, 2 * N, Rs...>(v, t, sm, tw2N);
+    stockham<R, N, E, INV, NL, TWS, 1, 2 * N, Rs...>(v, t, sm, tw2N);
 }
 
 }  // namespace pgb

@@ -169,8 +169,13 @@ template <class Cfg, int SLOTS, int LPT> constexpr int col_threads() {
 // placed there (ColFromSmem: element of tile row r at base[r * stride]).
 // The hook runs right after the inputs are in registers; the TMA kernel
 // uses it to start loading its next tile into the same buffer.
-struct ColFromGlobal {};
+// TW_SMEM: the tile's p.tw points to a copy of the axis twiddle table in
+// shared memory (the persistent TMA kernels), read with shared loads.
+struct ColFromGlobal {
+    static constexpr bool TW_SMEM = false;
+};
 template <class R> struct ColFromSmem {
+    static constexpr bool TW_SMEM = true;
     const cpx<R>* base;
     int stride;
 };
@@ -192,7 +197,7 @@ __device__ __forceinline__ cpx<R> col_in(const ColFromSmem<R>& s, const cpx<R>*,
 // two (each transform's last shared-memory read ends with a barrier, so the
 // next may write the buffer at once); otherwise both halves run in lockstep,
 // each through its own buffer.
-template <class Cfg, int SLOTS, int LPT, bool SEQ, bool INV>
+template <class Cfg, int SLOTS, int LPT, bool SEQ, bool INV, bool TWS = false>
 __device__ __forceinline__ void col_line_ffts(cpx<typename Cfg::R> (&v)[LPT][Cfg::E], const ColIds<Cfg, SLOTS, LPT>& id,
                                               cpx<typename Cfg::R>* sm, const cpx<typename Cfg::R>* tw) {
     using R = typename Cfg::R;
@@ -204,7 +209,7 @@ __device__ __forceinline__ void col_line_ffts(cpx<typename Cfg::R> (&v)[LPT][Cfg
             cpx<R> u[1][E];
 #pragma unroll
             for (int m = 0; m < E; ++m) u[0][m] = v[l][m];
-            line_fft<R, N, E, INV, 1>(u, id.t, l0, tw, typename Cfg::Rads{});
+            line_fft<R, N, E, INV, 1, TWS>(u, id.t, l0, tw, typename Cfg::Rads{});
 #pragma unroll
             for (int m = 0; m < E; ++m) v[l][m] = u[0][m];
         }
@@ -212,7 +217,7 @@ __device__ __forceinline__ void col_line_ffts(cpx<typename Cfg::R> (&v)[LPT][Cfg
         LineSmem<R> ls[LPT];
 #pragma unroll
         for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
-        line_fft<R, N, E, INV, LPT>(v, id.t, ls, tw, typename Cfg::Rads{});
+        line_fft<R, N, E, INV, LPT, TWS>(v, id.t, ls, tw, typename Cfg::Rads{});
     }
 }
 // exchange buffers a column tile needs
@@ -242,7 +247,7 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
-            const LineRamp<N, E, R> rw(p.tw, id.t);
+            const LineRamp<N, E, R, In::TW_SMEM> rw(p.tw, id.t);
             sfor<E>([&](auto m_) {
                 constexpr int m = decltype(m_)::value;
                 v[l][m] = cmul(v[0][m], rw.template at<m>());
@@ -252,7 +257,7 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
     LineSmem<R> ls[LPT];
 #pragma unroll
     for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
-    line_fft<R, N, E, false, LPT>(v, id.t, ls, p.tw, typename Cfg::Rads{});
+    line_fft<R, N, E, false, LPT, In::TW_SMEM>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
     if (c.valid) {
 #pragma unroll
@@ -270,14 +275,14 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
 // conj(a) and conj(b) (an inverse run as a conjugated forward transform),
 // and x = conj(conj(a) + W_2N^j conj(b)).  Returns true in the threads that
 // hold x[t + T m] in v[0][m] afterwards.
-template <class Cfg, int SLOTS, int LPT, bool CONJ = false>
+template <class Cfg, int SLOTS, int LPT, bool CONJ = false, bool TWS = false>
 __device__ __forceinline__ bool combine_halves(cpx<typename Cfg::R> (&v)[LPT][Cfg::E],
                                                const ColIds<Cfg, SLOTS, LPT>& id,
                                                cpx<typename Cfg::R>* sm,
                                                const cpx<typename Cfg::R>* tw) {
     using R = typename Cfg::R;
     constexpr int N = Cfg::N, E = Cfg::E, T = Cfg::T;
-    const LineRamp<N, E, R> rw(tw, id.t);
+    const LineRamp<N, E, R, TWS> rw(tw, id.t);
     if constexpr (LPT == 2) {
         sfor<E>([&](auto m_) {
             constexpr int m = decltype(m_)::value;
@@ -385,7 +390,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
 #pragma unroll
     for (int l = 0; l < LPT; ++l) {
         if (id.half(l)) {
-            const LineRamp<N, E, R> rw(p.tw, id.t);
+            const LineRamp<N, E, R, In::TW_SMEM> rw(p.tw, id.t);
             sfor<E>([&](auto m_) {
                 constexpr int m = decltype(m_)::value;
                 v[l][m] = cmul(v[0][m], rw.template at<m>());
@@ -399,7 +404,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
     // products and the combine conjugates back.
 #pragma unroll 1
     for (int ph = 0; ph < 2; ++ph) {
-        col_line_ffts<Cfg, SLOTS, LPT, SEQ, false>(v, id, sm, p.tw);
+        col_line_ffts<Cfg, SLOTS, LPT, SEQ, false, In::TW_SMEM>(v, id, sm, p.tw);
         if (ph == 1) break;
 
         // Green's multiply at frequency (kx, ky, kz), folded into the octant;
@@ -433,7 +438,7 @@ __device__ __forceinline__ void tile_z_conv(const PassParams<typename Cfg::R>& p
         }
     }
 
-    if (combine_halves<Cfg, SLOTS, LPT, true>(v, id, sm, p.tw) && c.valid) {
+    if (combine_halves<Cfg, SLOTS, LPT, true, In::TW_SMEM>(v, id, sm, p.tw) && c.valid) {
 #pragma unroll
         for (int m = 0; m < E; ++m) col[(long long)(id.t + T * m) * plane] = v[0][m];
     }
@@ -468,9 +473,9 @@ __device__ __forceinline__ void tile_y_inv(const PassParams<typename Cfg::R>& p,
                               : cpx<R>{0, 0};
     }
     after_load();
-    col_line_ffts<Cfg, SLOTS, LPT, SEQ, true>(v, id, sm, p.tw);
+    col_line_ffts<Cfg, SLOTS, LPT, SEQ, true, In::TW_SMEM>(v, id, sm, p.tw);
 
-    if (combine_halves<Cfg, SLOTS, LPT>(v, id, sm, p.tw) && c.valid) {
+    if (combine_halves<Cfg, SLOTS, LPT, false, In::TW_SMEM>(v, id, sm, p.tw) && c.valid) {
         cpx<R>* dst = out + (long long)c.other * ny * sx + c.kx + (long long)id.t * sx;
 #pragma unroll
         for (int m = 0; m < E; ++m) dst[(long long)(T * m) * sx] = v[0][m];
@@ -886,12 +891,19 @@ constexpr int kTmaWaitPolls = 1 << 20;  // bounded wait for one tile's copy
 
 template <int PASS, class Cfg, int SLOTS, int LPT, int MINB, int NBUF>
 __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
-    k_col_tma(PassParams<float> p, const __grid_constant__ CUtensorMap map, int t0, int t1, int hold) {
+    k_col_tma(PassParams<float> p, const __grid_constant__ CUtensorMap map, int t0, int t1, int hold, int tw_off,
+              int tw_n) {
     using B = TmaBox<PASS, Cfg, SLOTS, NBUF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<float>* buf = reinterpret_cast<cpx<float>*>(smem_raw);  // buffer k at buf + k * ROWS * SLOTS
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NBUF * B::BYTES);  // bar[0 .. NBUF)
     unsigned char* work = smem_raw + B::WORK_OFF;
+    // the axis twiddle table (tw_n entries), copied once per CTA behind the
+    // work area; the tiles read their twiddles from here
+    cpx<float>* tws = reinterpret_cast<cpx<float>*>(smem_raw + tw_off);
+    for (int i = threadIdx.x; i < tw_n; i += blockDim.x) tws[i] = ldg_c(p.tw + i);
+    PassParams<float> q = p;
+    q.tw = tws;
     const int lines = PASS == 2 ? 2 * p.ny : p.nz;
     const int wide_l = (lines + B::NLW - 1) / B::NLW;
     auto issue = [&](int tile, int k) {
@@ -942,9 +954,9 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
                 issue(next, k);
             }
         };
-        if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false>(p, tile, work, in, hook);
-        else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(p, tile, work, in, hook);
-        else tile_y_inv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(p, tile, work, in, hook);
+        if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false>(q, tile, work, in, hook);
+        else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(q, tile, work, in, hook);
+        else tile_y_inv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(q, tile, work, in, hook);
     }
 }
 
@@ -1039,7 +1051,10 @@ cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, i
     constexpr bool SEQ = NBUF == 1 && L == 2 && PASS != 1;
     constexpr size_t work = (SEQ ? col_smem<Cfg, S>() / 2 : col_smem<Cfg, S>()) +
                             (PASS == 2 ? col_smem_z<Cfg, S>() - col_smem<Cfg, S>() : 0);
-    constexpr size_t sm = B::WORK_OFF + work;
+    // behind the work area: the CTA's copy of the axis twiddle table
+    constexpr size_t tw_off = (B::WORK_OFF + work + 15) / 16 * 16;
+    constexpr int tw_n = tw_entries<Cfg::N>(typename Cfg::Rads{});
+    constexpr size_t sm = tw_off + (size_t)tw_n * sizeof(cpx<float>);
     // a tile whose buffers do not fit one CTA's shared memory, or whose box
     // would need more than 256 rows and several lines per box column, runs
     // every tile through the plain kernel instead
@@ -1075,7 +1090,7 @@ cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, i
         // test hook (failure detection without a GPU fault): the first copy of
         // every CTA is skipped, so its bounded wait runs out and reports
         const char* hold = std::getenv("POISSON_TEST_TMA_HOLD");
-        kern<<<grid, NT, sm, st>>>(p, map, t_begin, w1, hold && hold[0] == '1' ? 1 : 0);
+        kern<<<grid, NT, sm, st>>>(p, map, t_begin, w1, hold && hold[0] == '1' ? 1 : 0, (int)tw_off, tw_n);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int n0 = !fits ? t_begin : (t_begin > n_wide ? t_begin : n_wide);
