@@ -223,8 +223,11 @@ __device__ __forceinline__ void col_line_ffts(cpx<typename Cfg::R> (&v)[LPT][Cfg
 // exchange buffers a column tile needs
 template <int LPT, bool SEQ> constexpr int col_buffers() { return SEQ && LPT == 2 ? 1 : 2; }
 
-// pass 1: pad + forward FFT along y.  W1 -> W2.
-template <class Cfg, int SLOTS, int LPT, bool CG, class In = ColFromGlobal, class Hook = NoHook>
+// pass 1: pad + forward FFT along y.  W1 -> W2.  SEQ (two lines per
+// thread): the halves are transformed one after the other through one
+// exchange buffer, and each half is stored as soon as it is done, so the
+// even half's stores drain while the odd half is transformed.
+template <class Cfg, int SLOTS, int LPT, bool CG, bool SEQ = false, class In = ColFromGlobal, class Hook = NoHook>
 __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p, int tile,
                                             unsigned char* smem_raw, const In& in_src = In{},
                                             const Hook& after_load = Hook{}) {
@@ -254,18 +257,34 @@ __device__ __forceinline__ void tile_y_fwd(const PassParams<typename Cfg::R>& p,
             });
         }
     }
-    LineSmem<R> ls[LPT];
+    if constexpr (SEQ && LPT == 2) {
+        const LineSmem<R> l0[1] = {col_line<R, N, SLOTS>(sm, 0, id.slot)};
 #pragma unroll
-    for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
-    line_fft<R, N, E, false, LPT, In::TW_SMEM>(v, id.t, ls, p.tw, typename Cfg::Rads{});
+        for (int l = 0; l < 2; ++l) {
+            cpx<R> u[1][E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) u[0][m] = v[l][m];
+            line_fft<R, N, E, false, 1, In::TW_SMEM>(u, id.t, l0, p.tw, typename Cfg::Rads{});
+            if (c.valid) {
+                cpx<R>* dst = out + (long long)c.other * 2 * ny * sx + c.kx + (long long)(l * ny + id.t) * sx;
+#pragma unroll
+                for (int m = 0; m < E; ++m) dst[(long long)(T * m) * sx] = u[0][m];
+            }
+        }
+    } else {
+        LineSmem<R> ls[LPT];
+#pragma unroll
+        for (int l = 0; l < LPT; ++l) ls[l] = col_line<R, N, SLOTS>(sm, id.half(l), id.slot);
+        line_fft<R, N, E, false, LPT, In::TW_SMEM>(v, id.t, ls, p.tw, typename Cfg::Rads{});
 
-    if (c.valid) {
+        if (c.valid) {
 #pragma unroll
-        for (int l = 0; l < LPT; ++l) {
-            cpx<R>* dst = out + (long long)c.other * 2 * ny * sx + c.kx +
-                          (long long)(id.half(l) * ny + id.t) * sx;
+            for (int l = 0; l < LPT; ++l) {
+                cpx<R>* dst = out + (long long)c.other * 2 * ny * sx + c.kx +
+                              (long long)(id.half(l) * ny + id.t) * sx;
 #pragma unroll
-            for (int m = 0; m < E; ++m) dst[(long long)(T * m) * sx] = v[l][m];
+                for (int m = 0; m < E; ++m) dst[(long long)(T * m) * sx] = v[l][m];
+            }
         }
     }
 }
@@ -954,7 +973,7 @@ __global__ void __launch_bounds__(col_threads<Cfg, SLOTS, LPT>(), MINB)
                 issue(next, k);
             }
         };
-        if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false>(q, tile, work, in, hook);
+        if constexpr (PASS == 1) tile_y_fwd<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(q, tile, work, in, hook);
         else if constexpr (PASS == 2) tile_z_conv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(q, tile, work, in, hook);
         else tile_y_inv<Cfg, SLOTS, LPT, false, NBUF == 1 && LPT == 2>(q, tile, work, in, hook);
     }
@@ -1046,9 +1065,9 @@ template <int PASS, class Cfg, int S, int L, int MINB, int NBUF>
 cudaError_t launch_col_tma(const PassParams<float>& p, int t_begin, int t_end, int n_wide, cudaStream_t st) {
     using B = TmaBox<PASS, Cfg, S, NBUF>;
     constexpr int NT = col_threads<Cfg, S, L>();
-    // (the single-buffered z and inverse y tiles transform their halves one
-    // after the other through one exchange buffer)
-    constexpr bool SEQ = NBUF == 1 && L == 2 && PASS != 1;
+    // (the single-buffered tiles transform their halves one after the other
+    // through one exchange buffer)
+    constexpr bool SEQ = NBUF == 1 && L == 2;
     constexpr size_t work = (SEQ ? col_smem<Cfg, S>() / 2 : col_smem<Cfg, S>()) +
                             (PASS == 2 ? col_smem_z<Cfg, S>() - col_smem<Cfg, S>() : 0);
     // behind the work area: the CTA's copy of the axis twiddle table
